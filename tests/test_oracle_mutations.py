@@ -1,0 +1,49 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (a wrong
+stencil coefficient, a flipped sign, a dropped term, a transposed axis, a
+missing factor), builds it into a temporary library, and runs the pin tests
+against it in a subprocess; the pins must fail.  Nothing here touches a GPU.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mlmd_oracle.c")
+
+MUTANTS = [
+    ("laplacian centre coefficient", "lap[0] = -2.5;", "lap[0] = -2.4;"),
+    ("gradient outer coefficient sign", "grad[2] = -1.0 / 12.0;", "grad[2] = 1.0 / 12.0;"),
+    ("sign of the A.grad term", "- I * ih * ag", "+ I * ih * ag"),
+    ("dropped |A|^2/2 term", "(d->V[g] + a2) * c", "(d->V[g]) * c"),
+    ("missing dV in the projection", "proj[((int64_t)a * np + i) * no + o] *= dV;", ";"),
+    ("missing D in the scatter", "d->D[(int64_t)a * np + i] * proj", "proj"),
+    ("Taylor coefficient without 1/j!", "c *= (-I * dt) / (double)j;", "c *= (-I * dt);"),
+    ("p projector on the wrong axis", "beta[q * n_proj + 4 * set + 1 + ax] = dl[ax]",
+     "beta[q * n_proj + 4 * set + 1 + ax] = dl[(ax + 1) % 3]"),
+    ("minimum image without the half shift", "double k = floor(t / L[ax] + 0.5);", "double k = floor(t / L[ax]);"),
+    ("current without the A rho term", "jcur[ax * ng + g] = s + A[ax] * rho[g];", "jcur[ax * ng + g] = s;"),
+    ("adjoint Taylor with the forward sign", "c *= (I * dt) / (double)j;", "c *= (-I * dt) / (double)j;"),
+    ("energy without the nonlocal part", "orc_apply_h(d, A, psi_in, work, work_proj);\n    for (int64_t g = 0; g < ng; ++g)\n        for (int o = 0; o < no; ++o) {\n            cplx c = in[g * no + o];\n            nrm",
+     "orc_apply_hloc(d, A, psi_in, work);\n    for (int64_t g = 0; g < ng; ++g)\n        for (int o = 0; o < no; ++o) {\n            cplx c = in[g * no + o];\n            nrm"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, tmp_path):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique: {name}"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+                           "-o", str(so), str(mutated), "-lm"])
+    env = dict(os.environ, MLMD_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
