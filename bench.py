@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the LFD propagation hot path on one GB300 (or N replicas).
+
+Workload (the c1 domain): 48^3 periodic grid, h = 0.35 bohr, 256 complex64
+Kohn-Sham orbitals, 4th-order finite differences, 64 Gaussian wells on a
+perturbed 4x4x4 lattice, 64 atoms x 4 projectors (r_c = 1.2, r_cut = 3),
+Gaussian-envelope vector potential, f_n = 2.  One benchmark step is one
+mlmd_propagate call of 1000 full-scheme Taylor-4 steps with per-step
+observables (electron count, energy, current), plus the density/current
+fields of the final state.  Metric: orbital*gridpoint*steps per second
+(units = N_o * N_g * Taylor steps); also seconds per (electron * step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "orbital·gridpoint·steps/s per GB300"
+UNIT = "orbital·gridpoint·steps/s"
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic HBM bytes per orbital*gridpoint*step of the four staged
+# full-scheme passes in complex64: the first reads psi and writes w (16 B),
+# the other three read w and psi and write w or psi (24 B each)
+STAGE_BYTES_PER_UNIT = 16 + 3 * 24
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--qd-steps", type=int, default=1000, help="Taylor steps per benchmark step")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    return p.parse_args()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) of one GPU while the timed region runs."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                smax.append(float(c[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(qd_steps):
+    from paper_2509_00966_gb300 import inputs
+    spec = inputs.config("c1")
+    A = inputs.envelope_pulse(1000, spec.dt)
+    reps = (qd_steps + 999) // 1000
+    spec.A = np.tile(A, (reps, 1))[:qd_steps]
+    spec.n_steps = qd_steps
+    V = inputs.gaussian_wells(spec.n, spec.h, spec.wells, spec.well_depth, spec.well_width)
+    psi = inputs.random_orbitals(spec.n_grid, spec.n_orb, spec.dV, spec.seed)
+    return spec, V, psi
+
+
+def _workload_name(spec, qd):
+    return (f"c1: {spec.n[0]}^3 grid h={spec.h} bohr, {spec.n_orb} complex64 orbitals, {spec.fd_order}th-order FD, "
+            f"{len(spec.atoms)} atoms x {spec.n_proj} projectors, Gaussian-envelope A(t), {qd} full-scheme "
+            f"Taylor-4 steps + per-step norm/energy/current per bench step")
+
+
+def oracle_sample(spec, V, psi, target_s, max_steps=20):
+    """Time the FP64 oracle (as it stands) on the benchmark workload: all
+    orbitals, the full grid, a few Taylor steps with observables."""
+    import oracle
+    od = oracle.Domain(spec.n, spec.h, spec.n_orb, spec.fd_order, V, spec.atoms, spec.n_proj, spec.r_c, spec.r_cut,
+                       spec.D)
+    f = np.full(spec.n_orb, 2.0)
+    p = psi.astype(np.complex128)
+    t0 = time.perf_counter()
+    p, _ = oracle.propagate(od, p, spec.A[:1], spec.dt, f)
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(max_steps, round(target_s / max(t1, 1e-3)) - 1)))
+    t0 = time.perf_counter()
+    p, _ = oracle.propagate(od, p, spec.A[1:1 + n], spec.dt, f)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    units = spec.n_grid * spec.n_orb * n
+    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} Taylor-4 steps (+observables) of the full workload, all {spec.n_orb} orbitals, "
+                      f"FP64 C/OpenMP oracle, {dt:.1f} s"}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _physical_gpu(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local < len(ids):
+            return ids[local]
+    return str(local)
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is one Taylor step of the
+    same workload on the host cores (rank 0 only)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    spec, V, psi = _workload(max(args.steps + args.warmup, 1))
+    od = oracle.Domain(spec.n, spec.h, spec.n_orb, spec.fd_order, V, spec.atoms, spec.n_proj, spec.r_c, spec.r_cut,
+                       spec.D)
+    f = np.full(spec.n_orb, 2.0)
+    p = psi.astype(np.complex128)
+    for k in range(args.warmup):
+        p, _ = oracle.propagate(od, p, spec.A[k:k + 1], spec.dt, f)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        p, _ = oracle.propagate(od, p, spec.A[k:k + 1], spec.dt, f)
+    dt = time.perf_counter() - t0
+    units = spec.n_grid * spec.n_orb * args.steps
+    v = units / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded PbTiO3-like domain)",
+            "config": {"workload": _workload_name(spec, 1), "reference_step": "1 Taylor-4 step with observables",
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} Taylor steps of the full workload, FP64 C/OpenMP oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2509_00966_gb300 import build, mlmd
+    build.build()
+    spec, V, psi = _workload(args.qd_steps)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(spec, V, psi, args.cpu_seconds)
+
+    dom = mlmd.Domain.from_spec(spec, V=V)
+    psi_dev = torch.from_numpy(psi).to(torch.complex64).cuda()
+    dom.set_orbitals(psi_dev)
+    A = spec.A
+    A_last = A[-1]
+
+    def one_step():
+        obs = dom.propagate(A, obs=True)
+        dom.density_current(A_last)
+        return obs
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(_physical_gpu(local))
+    clocks.start()
+    time.sleep(0.3)
+    mlmd.profile_enable(dom.handle, True)
+    l0 = dom.launches
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        obs = one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    launches = dom.launches - l0
+    st_ms, st_n = mlmd.profile_read(dom.handle, "stage")
+    pr_ms, pr_n = mlmd.profile_read(dom.handle, "project")
+    mlmd.profile_enable(dom.handle, False)
+    ck = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+        torch.distributed.barrier()
+
+    # end to end through the C ABI with host buffers: h2d of the orbitals,
+    # the propagation, d2h of the orbitals and observables, every step
+    pinned_in = torch.from_numpy(psi.astype(np.complex64)).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    e2e_t = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dom.set_orbitals(pinned_in)
+        dom.propagate(A, obs=True)
+        mlmd.get_orbitals(dom.handle, pinned_out)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_t)) if e2e_t else float("nan")
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    units_step = spec.n_grid * spec.n_orb * args.qd_steps
+    value = ws * units_step * args.steps / (t_ms * 1e-3)
+    electrons = float(np.sum(spec.occ))
+    t2s = (t_ms * 1e-3) / (args.steps * args.qd_steps * electrons)
+    peak, peak_src = _peaks()
+    stage_units = st_n / 4 * spec.n_grid * spec.n_orb   # four stage launches per Taylor step
+    achieved = STAGE_BYTES_PER_UNIT * stage_units / (st_ms * 1e-3) / 1e9 if st_ms > 0 else None
+    dom.close()
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded PbTiO3-like domain, random orthonormal orbitals)",
+        "config": {"workload": _workload_name(spec, args.qd_steps), "n_grid": spec.n_grid, "n_orb": spec.n_orb,
+                   "qd_steps_per_step": args.qd_steps, "scheme": "full (v_nl inside Taylor-4)",
+                   "l2": "inputs larger than L2 (psi 226 MB + two work states > 129 MB), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "t2s_s_per_electron_step": t2s,
+        "t2s_paper_context": "1.11e-7 s/(electron*step) on 120,000 PVC tiles (paper, other hardware; context only)",
+        "roofline": {"bound": "hbm", "kernel": "k_stage (fused stencil + V + A + scatter + Taylor combine)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "peak_source": f"{peak_src} hbm_gbs",
+                     "bytes_per_unit_step": STAGE_BYTES_PER_UNIT, "traffic": None,
+                     "kernel_share": {"stage": st_ms / t_ms, "project": pr_ms / t_ms},
+                     "launches": {"stage": st_n, "project": pr_n}},
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * units_step / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(psi.size * 8 + A.size * 8),
+                "d2h_bytes_per_step": int(psi.size * 8 + args.qd_steps * 5 * 8)},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

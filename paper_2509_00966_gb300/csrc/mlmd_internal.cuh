@@ -1,0 +1,214 @@
+// Internal declarations of libmlmd (CUDA, sm_103a).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "mlmd.h"
+
+namespace mlmd {
+
+// ---------------------------------------------------------------------------
+// error plumbing: every entry point converts failures into an mlmd_status
+// ---------------------------------------------------------------------------
+struct Error {
+    mlmd_status status;
+    std::string msg;
+};
+
+#define MLMD_CUDA(call)                                                                      \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            throw ::mlmd::Error{MLMD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define MLMD_REQUIRE(cond, code, text)                                      \
+    do {                                                                    \
+        if (!(cond)) throw ::mlmd::Error{code, std::string(text)};          \
+    } while (0)
+
+// Padded orbital stride: orbitals are stored in rows of `ld` complex values
+// with ld a multiple of 8 (64-byte rows for complex64), padding orbitals zero.
+inline int padded_orbitals(int n_orb) { return (n_orb + 7) / 8 * 8; }
+
+// ---------------------------------------------------------------------------
+// device memory through the caller's allocator or cudaMallocAsync
+// ---------------------------------------------------------------------------
+struct Alloc {
+    mlmd_allocator a{};
+    bool custom = false;
+    cudaStream_t stream = nullptr;
+    struct Blk { void* p; size_t bytes; };
+    std::vector<Blk> live;
+
+    void* get(size_t bytes);
+    void put(void* p);
+    void release_all();
+};
+
+// Projector tables built on the device by set_projectors.
+struct Nonlocal {
+    int n_atoms = 0;
+    int n_proj = 0;
+    int64_t n_list = 0;            // total (atom, point) entries
+    int max_count = 0;             // longest atom list
+    int64_t* off = nullptr;        // [n_atoms + 1] list offsets
+    int32_t* idx = nullptr;        // [n_list] grid index, ascending per atom
+    double* beta64 = nullptr;      // [n_list][n_proj] FP64 projector values
+    void* beta = nullptr;          // [n_list][n_proj] in the working real type
+    int32_t* pstart = nullptr;     // [N_g + 1] per-point entry ranges
+    int32_t* patom = nullptr;      // [n_list] atom of each per-point entry
+    void* pbd = nullptr;           // [n_list][n_proj] beta * D (working real type)
+    double* D = nullptr;           // [n_atoms][n_proj]
+    std::vector<int64_t> h_off;    // host copy of off
+    int n_seg = 0;                 // projection segments per atom
+    int seg_len = 0;
+};
+
+// CUDA-event timing of selected kernel kinds (enabled by mlmd_profile_enable).
+struct Profiler {
+    bool on = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double total_ms[MLMD_KERNEL_KINDS] = {0.0, 0.0};
+    uint64_t count[MLMD_KERNEL_KINDS] = {0, 0};
+    cudaEvent_t take();
+    void begin(int kind, cudaStream_t s, Rec& r);
+    void end(Rec& r, cudaStream_t s);
+    void collect();              // caller synchronised the stream
+    void reset();
+    void destroy();
+};
+
+// RAII bracket around one launch of a timed kind.
+struct ProfScope {
+    Profiler& p;
+    cudaStream_t s;
+    Profiler::Rec r{};
+    bool on;
+    ProfScope(Profiler& pp, int kind, cudaStream_t st) : p(pp), s(st), on(pp.on) { if (on) p.begin(kind, s, r); }
+    ~ProfScope() { if (on) p.end(r, s); }
+};
+
+struct Domain {
+    mlmd_domain_desc desc{};
+    int64_t ng = 0;                // grid points
+    int ld = 0;                    // padded orbital stride
+    size_t elem = 0;               // bytes per complex value
+    size_t state_bytes = 0;        // ng * ld * elem
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Alloc mem;
+
+    void* psi = nullptr;           // current orbitals
+    void* psi0 = nullptr;          // reference orbitals Psi(0)
+    void* wa = nullptr;            // Taylor work buffers
+    void* wb = nullptr;
+    void* V = nullptr;             // [ng] local potential (working real type)
+    double* V64 = nullptr;         // [ng] FP64 copy (adjoint, batch)
+    double* f = nullptr;           // [ld] occupations, zero on padding
+    Nonlocal nl;
+    void* Pa = nullptr;            // projections [n_atoms][n_proj][ld] complex
+    void* Pb = nullptr;
+    void* Pseg = nullptr;          // segment partials [n_seg][n_atoms][n_proj][ld]
+    double* obs_part = nullptr;    // per-block observable partials
+    int obs_blocks = 0;
+    double* obs_dev = nullptr;     // [cap][5]
+    int obs_cap = 0;
+    double* A_dev = nullptr;       // [cap][3]
+    int A_cap = 0;
+    double* dense = nullptr;       // scratch for N_o x N_o FP64 work
+    size_t dense_bytes = 0;
+
+    int64_t step = 0;              // steps since set_orbitals
+    bool psi0_valid = false;
+    uint64_t launches = 0;
+    Profiler prof;
+    mlmd_status latched = MLMD_OK;
+    std::string err;
+
+    bool c64() const { return desc.precision == MLMD_C64; }
+    bool has_nl() const { return nl.n_atoms > 0 && nl.n_proj > 0; }
+};
+
+// ---------------------------------------------------------------------------
+// kernels (launch wrappers count launches into dom.launches)
+// ---------------------------------------------------------------------------
+
+// out = psi + gamma * (h(A) w) with h of Eq. 3; psi may be null (then out =
+// gamma * h w).  P: projections of w (may be null when there are no
+// projectors).  When obs != null, also writes per-block partial observables
+// of w (which must then equal psi's state) into obs.
+struct StageArgs {
+    const void* w;
+    const void* psi;
+    void* out;
+    const void* P;
+    const double* A;               // device [3]
+    double gamma_re, gamma_im;
+    double* obs;                   // per-block partials [blocks][5] or null
+};
+void launch_stage(Domain& d, const StageArgs& a);
+int stage_blocks(const Domain& d);
+
+// P[a][i][o] = dV sum_q beta[q][i] w[idx[q]][o]
+void launch_project(Domain& d, const void* w, void* P);
+
+// obs_dev[row][0..4] = final observables from the per-block partials
+void launch_obs_finish(Domain& d, const double* partials, int nblocks, const double* A, double* row);
+
+// density / current
+void launch_density_current(Domain& d, const double* A, void* rho, void* j, double* Jpart, int nblk);
+int density_blocks(const Domain& d);
+
+// out = sum_t coef[t] * in[t] over whole states (t < n <= 5)
+void launch_lincomb(Domain& d, int n, const void* const* in, const double* coef_re, const double* coef_im,
+                    void* out);
+
+// adjoint contractions: for p < 4, with z_p, u_p states:
+//   gA[a]  += 2 Re sum <z_p | -i G_a u_p>   (per-block partials, a = 0..2)
+//   gZ     += 2 Re sum <z_p | u_p>           (partial index 3)
+//   gV[r]  += 2 Re sum_o conj(z_p) u_p       (FP64 [ng], accumulated)
+void launch_adjoint_contract(Domain& d, const void* const* z, const void* const* u, double* part, int nblk,
+                             double* gV);
+int contract_blocks(const Domain& d);
+
+// neighbour lists and projector tables (a1)
+void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj, double r_c, double r_cut,
+                      const double* D_host);
+
+// dense orbital-space algebra (FP64 results)
+// S[n][m] = scale * sum_g conj(X[g][n]) Y[g][m] for n, m < n_orb; S is
+// complex double [n_orb][n_orb] on the device.
+void launch_overlap(Domain& d, const void* X, const void* Y, double scale, double* S);
+// Y[g][m] = sum_n X[g][n] M[n][m] (M complex double [n_orb][n_orb], device)
+void launch_update(Domain& d, const void* X, const double* M, void* Y);
+// In place: S -> lower Cholesky factor L (S = L L^H); returns false if S is
+// not positive definite.  Then Minv = L^{-H} (upper).
+void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info);
+// Minv = S^{-1/2} by coupled Newton-Schulz iterations in FP64.
+void lowdin_inverse_sqrt(Domain& d, double* S, double* Minv, double* work, int* d_info);
+
+// One full-scheme Taylor-4 step of the domain's orbitals under A (device
+// [3]); writes the pre-step observables to obs_row (device [5]) if non-null.
+// Allocates nothing, so it can be captured into a CUDA graph.
+void step_full(Domain& d, const double* Ak, double* obs_row);
+
+// final reduce of per-block partials (fixed order, FP64)
+void launch_reduce_partials(Domain& d, const double* part, int nblk, int width, double* out);
+
+}  // namespace mlmd
+
+// The opaque handles of the ABI.
+struct mlmd_domain : public mlmd::Domain {};
+
+struct mlmd_batch {
+    std::vector<mlmd_domain*> doms;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+};
