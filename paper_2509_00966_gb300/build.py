@@ -70,6 +70,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    # every symbol of the library's own namespace must be defined in it
+    nm = subprocess.run(["nm", "-D", "--undefined-only", tmp], capture_output=True, text=True)
+    missing = [l.split()[-1] for l in nm.stdout.splitlines() if "mlmd" in l]
+    if missing:
+        os.unlink(tmp)
+        raise RuntimeError(f"libmlmd link left undefined symbols: {missing}")
     os.replace(tmp, LIB)
     return LIB
 

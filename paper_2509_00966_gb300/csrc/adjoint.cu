@@ -89,6 +89,7 @@ extern "C" mlmd_status mlmd_propagate_adjoint(mlmd_domain_t dom, int32_t n_steps
         MLMD_REQUIRE(d->psi0_valid, MLMD_ERR_STATE, "no reference orbitals (call mlmd_set_orbitals)");
         for (int i = 0; i < 3 * n_steps; ++i) MLMD_REQUIRE(std::isfinite(A[i]), MLMD_ERR_INVALID, "A not finite");
         Scratch S(*d);
+        d->pa_psi = false;
         const size_t sb = d->state_bytes;
         const int K = ckpt_every;
         const int nck = (n_steps + K - 1) / K;

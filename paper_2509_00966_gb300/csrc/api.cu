@@ -58,28 +58,40 @@ void Alloc::release_all() {
 // One FULL-scheme Taylor-4 step in nested form:
 //   w <- psi + (-i dt/4) h psi;  w <- psi + (-i dt/3) h w;
 //   w <- psi + (-i dt/2) h w;    psi <- psi + (-i dt) h w
-// each h = local stencil + fused scatter of the projections of its input.
+// each h = local stencil + scatter-back of the projections of its input.
+// When the TMA stage kernel fuses the projection of its output, the four
+// stages pass the projections along (Pa -> Pb -> Pa -> Pb -> Pa) and Pa holds
+// <b|psi> of the new orbitals for the next step; otherwise each stage is
+// preceded by a projection pass over its input.
 void step_full(Domain& d, const double* Ak, double* obs_row) {
     const double dt = d.desc.dt;
     const bool nl = d.has_nl();
+    const bool fused = nl && tma_fused_nl(d);
+    if (fused && !d.pa_psi) launch_project(d, d.psi, d.Pa);
     const void* in = d.psi;
     void* outs[4] = {d.wa, d.wb, d.wa, d.psi};
-    void* Ps[4] = {d.Pa, d.Pb, d.Pa, d.Pb};
+    void* Pin[4] = {d.Pa, d.Pb, d.Pa, d.Pb};
+    void* Pout[4] = {d.Pb, d.Pa, d.Pb, d.Pa};
+    bool chain = fused;
     for (int s = 0; s < 4; ++s) {
-        if (nl) launch_project(d, in, Ps[s]);
+        if (nl && !chain) launch_project(d, in, Pin[s]);
         StageArgs a;
         a.w = in;
         a.psi = d.psi;
         a.out = outs[s];
-        a.P = nl ? Ps[s] : nullptr;
+        a.P = nl ? Pin[s] : nullptr;
+        a.P_out = fused ? Pout[s] : nullptr;
         a.A = Ak;
         a.gamma_re = 0.0;
         a.gamma_im = -dt / (double)(4 - s);
         a.obs = (s == 0 && obs_row) ? d.obs_part : nullptr;
-        launch_stage(d, a);
-        if (s == 0 && obs_row) launch_obs_finish(d, d.obs_part, d.obs_blocks, Ak, obs_row);
+        bool done = false;
+        const int nblk = launch_stage(d, a, &done);
+        chain = fused && done;
+        if (s == 0 && obs_row) launch_obs_finish(d, d.obs_part, nblk, Ak, obs_row);
         in = outs[s];
     }
+    d.pa_psi = chain;
 }
 
 // ---------------------------------------------------------------------------
@@ -194,8 +206,8 @@ void apply_h(Domain& d, const void* in, void* out, const double* Ak, double* obs
     a.gamma_re = 1.0;
     a.gamma_im = 0.0;
     a.obs = obs_row ? d.obs_part : nullptr;
-    launch_stage(d, a);
-    if (obs_row) launch_obs_finish(d, d.obs_part, d.obs_blocks, Ak, obs_row);
+    const int nblk = launch_stage(d, a);
+    if (obs_row) launch_obs_finish(d, d.obs_part, nblk, Ak, obs_row);
 }
 
 void reorth(Domain& d, int kind);
@@ -223,6 +235,7 @@ void apply_nnl(Domain& d) {
 }
 
 void step_split(Domain& d, const double* Ak, double* obs_row) {
+    d.pa_psi = false;
     if (obs_row) apply_h(d, d.psi, d.wb, Ak, obs_row);
     if (d.has_nl()) apply_nnl(d);
     const double dt = d.desc.dt;
@@ -245,6 +258,7 @@ void step_split(Domain& d, const double* Ak, double* obs_row) {
 }
 
 void reorth(Domain& d, int kind) {
+    d.pa_psi = false;
     const int n = d.desc.n_orb;
     const size_t mat = (size_t)n * n * 2;
     double* base = ensure_dense(d, mat * (kind == MLMD_ORTHO_LOWDIN ? 6 : 2) + 8);
@@ -263,6 +277,19 @@ void reorth(Domain& d, int kind) {
     std::swap(d.psi, d.wa);
 }
 
+// f (padded to ld with zeros) into the FP64 and working-type copies.
+void upload_occupations(Domain& d, const std::vector<double>& f) {
+    MLMD_CUDA(cudaMemcpyAsync(d.f, f.data(), sizeof(double) * d.ld, cudaMemcpyHostToDevice, d.stream));
+    if (d.c64()) {
+        std::vector<float> ff(f.begin(), f.end());
+        MLMD_CUDA(cudaMemcpyAsync(d.fR, ff.data(), sizeof(float) * d.ld, cudaMemcpyHostToDevice, d.stream));
+        MLMD_CUDA(cudaStreamSynchronize(d.stream));
+    } else {
+        MLMD_CUDA(cudaMemcpyAsync(d.fR, f.data(), sizeof(double) * d.ld, cudaMemcpyHostToDevice, d.stream));
+        MLMD_CUDA(cudaStreamSynchronize(d.stream));
+    }
+}
+
 void check_desc(const mlmd_domain_desc* s) {
     MLMD_REQUIRE(s != nullptr, MLMD_ERR_INVALID, "null descriptor");
     for (int i = 0; i < 3; ++i) MLMD_REQUIRE(s->n[i] >= 4 && s->n[i] <= 4096, MLMD_ERR_INVALID, "grid size out of range");
@@ -278,6 +305,8 @@ void check_desc(const mlmd_domain_desc* s) {
                  "bad ortho_kind");
     const int64_t ng = (int64_t)s->n[0] * s->n[1] * s->n[2];
     MLMD_REQUIRE(ng < ((int64_t)1 << 31), MLMD_ERR_INVALID, "grid too large");
+    const int64_t nv = (int64_t)(s->n_orb + 7) / 8 * 8 / (s->precision == MLMD_C64 ? 2 : 1);
+    MLMD_REQUIRE((int64_t)s->n[0] * nv < ((int64_t)1 << 31), MLMD_ERR_INVALID, "grid line too long");
 }
 
 }  // namespace
@@ -334,15 +363,18 @@ mlmd_status mlmd_domain_create(const mlmd_domain_desc* desc, const mlmd_allocato
         d->V = d->mem.get(rsz * d->ng);
         d->V64 = (double*)d->mem.get(sizeof(double) * d->ng);
         d->f = (double*)d->mem.get(sizeof(double) * d->ld);
+        d->fR = d->mem.get(rsz * d->ld);
         d->obs_blocks = stage_blocks(*d);
+        d->err_flag = (int*)d->mem.get(sizeof(int));
+        MLMD_CUDA(cudaMemsetAsync(d->err_flag, 0, sizeof(int), d->stream));
+        tma_setup(*d);
         d->obs_part = (double*)d->mem.get(sizeof(double) * 5 * (size_t)std::max(d->obs_blocks, density_blocks(*d) * 2));
         MLMD_CUDA(cudaMemsetAsync(d->psi, 0, d->state_bytes, d->stream));
         MLMD_CUDA(cudaMemsetAsync(d->V, 0, rsz * d->ng, d->stream));
         MLMD_CUDA(cudaMemsetAsync(d->V64, 0, sizeof(double) * d->ng, d->stream));
         std::vector<double> f(d->ld, 0.0);
         for (int i = 0; i < desc->n_orb; ++i) f[i] = 2.0;
-        MLMD_CUDA(cudaMemcpyAsync(d->f, f.data(), sizeof(double) * d->ld, cudaMemcpyHostToDevice, d->stream));
-        MLMD_CUDA(cudaStreamSynchronize(d->stream));
+        upload_occupations(*d, f);
     });
     if (st != MLMD_OK) {
         d->mem.release_all();
@@ -359,6 +391,7 @@ mlmd_status mlmd_domain_destroy(mlmd_domain_t dom) {
     dom->mem.release_all();
     cudaError_t e = cudaStreamSynchronize(dom->stream);
     dom->prof.destroy();
+    tma_release(*dom);
     delete dom;
     return e == cudaSuccess ? MLMD_OK : MLMD_ERR_CUDA;
 }
@@ -366,6 +399,7 @@ mlmd_status mlmd_domain_destroy(mlmd_domain_t dom) {
 mlmd_status mlmd_set_orbitals(mlmd_domain_t d, const void* psi, int32_t on_device) {
     return guarded(d, [&] {
         MLMD_REQUIRE(psi != nullptr, MLMD_ERR_INVALID, "null orbitals");
+        d->pa_psi = false;
         const size_t src_pitch = (size_t)d->desc.n_orb * d->elem, dst_pitch = (size_t)d->ld * d->elem;
         MLMD_CUDA(cudaMemsetAsync(d->psi, 0, d->state_bytes, d->stream));
         MLMD_CUDA(cudaMemcpy2DAsync(d->psi, dst_pitch, psi, src_pitch, src_pitch, (size_t)d->ng,
@@ -396,8 +430,7 @@ mlmd_status mlmd_set_occupations(mlmd_domain_t d, const double* f) {
             MLMD_REQUIRE(std::isfinite(f[i]), MLMD_ERR_INVALID, "occupation not finite");
             h[i] = f[i];
         }
-        MLMD_CUDA(cudaMemcpyAsync(d->f, h.data(), sizeof(double) * d->ld, cudaMemcpyHostToDevice, d->stream));
-        MLMD_CUDA(cudaStreamSynchronize(d->stream));
+        upload_occupations(*d, h);
     });
 }
 
@@ -471,8 +504,11 @@ mlmd_status mlmd_propagate(mlmd_domain_t d, int32_t n_steps, const double* A, do
         if (obs_out) {
             MLMD_CUDA(cudaMemcpyAsync(obs_out, d->obs_dev, sizeof(double) * 5 * n_steps, cudaMemcpyDeviceToHost, d->stream));
         }
+        int h_err = 0;
+        MLMD_CUDA(cudaMemcpyAsync(&h_err, d->err_flag, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
         MLMD_CUDA(cudaStreamSynchronize(d->stream));
         MLMD_CUDA(cudaGetLastError());
+        MLMD_REQUIRE(h_err == 0, MLMD_ERR_TIMEOUT, "a device-side wait timed out");
         if (obs_out)
             for (int i = 0; i < 5 * n_steps; ++i)
                 MLMD_REQUIRE(std::isfinite(obs_out[i]), MLMD_ERR_NUMERIC, "observable is NaN or Inf");

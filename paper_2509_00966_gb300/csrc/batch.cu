@@ -92,26 +92,68 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         MLMD_CUDA(cudaMemcpyAsync(A_all, A, sizeof(double) * 3 * (size_t)nd * n_steps, cudaMemcpyHostToDevice, st));
         MLMD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), st));
         MLMD_CUDA(cudaMemsetAsync(obs_cur, 0, sizeof(double) * 5 * nd, st));
+        // projections of the current orbitals, outside the graph, so that the
+        // captured step is the steady-state one
+        for (auto* d : b->doms)
+            if (d->has_nl() && tma_fused_nl(*d) && !d->pa_psi) {
+                launch_project(*d, d->psi, d->Pa);
+                d->pa_psi = true;
+            }
         MLMD_CUDA(cudaStreamSynchronize(st));
-        // capture one step of every domain
-        MLMD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        // Capture one step of every domain on a private stream (the legacy
+        // default stream cannot be captured), ordered after the caller's
+        // stream by an event and joined back the same way.
+        cudaStream_t cap = nullptr;
+        cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+        MLMD_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        MLMD_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+        MLMD_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+        struct Restore {
+            std::vector<mlmd_domain*>& ds;
+            cudaStream_t orig, cap;
+            cudaEvent_t a, b;
+            ~Restore() {
+                for (auto* d : ds) { d->stream = orig; d->mem.stream = orig; }
+                (void)cudaStreamSynchronize(cap);
+                (void)cudaStreamDestroy(cap);
+                (void)cudaEventDestroy(a);
+                (void)cudaEventDestroy(b);
+            }
+        } restore{b->doms, st, cap, ev_in, ev_out};
+        std::vector<uint64_t> before;
+        std::vector<bool> prof_on;
+        for (auto* d : b->doms) {
+            d->stream = cap;
+            d->mem.stream = cap;
+            before.push_back(d->launches);
+            prof_on.push_back(d->prof.on);
+            d->prof.on = false;   // no timing events inside the graph
+        }
+        MLMD_CUDA(cudaEventRecord(ev_in, st));
+        MLMD_CUDA(cudaStreamWaitEvent(cap, ev_in, 0));
+        MLMD_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         try {
-            k_batch_begin<<<(nd * 3 + 255) / 256, 256, 0, st>>>(nd, n_steps, A_all, ctr, A_cur);
+            k_batch_begin<<<(nd * 3 + 255) / 256, 256, 0, cap>>>(nd, n_steps, A_all, ctr, A_cur);
             for (int i = 0; i < nd; ++i)
                 step_full(*b->doms[i], A_cur + 3 * i, obs_out ? obs_cur + 5 * i : nullptr);
-            k_batch_end<<<1, 256, 0, st>>>(nd, n_steps, obs_cur, ctr, obs_all);
+            k_batch_end<<<1, 256, 0, cap>>>(nd, n_steps, obs_cur, ctr, obs_all);
         } catch (...) {
             cudaGraph_t g = nullptr;
-            (void)cudaStreamEndCapture(st, &g);
+            (void)cudaStreamEndCapture(cap, &g);
             if (g) (void)cudaGraphDestroy(g);
             throw;
         }
-        MLMD_CUDA(cudaStreamEndCapture(st, &graph));
+        MLMD_CUDA(cudaStreamEndCapture(cap, &graph));
         MLMD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-        for (int k = 0; k < n_steps; ++k) MLMD_CUDA(cudaGraphLaunch(exec, st));
-        for (auto* d : b->doms) d->launches += 0;  // counted at capture
-        d0.launches += 2ull * n_steps;
-        // each captured kernel runs once per replay
+        // every captured kernel runs once per replay
+        for (int i = 0; i < nd; ++i) {
+            const uint64_t captured = b->doms[i]->launches - before[i];
+            b->doms[i]->launches = before[i] + captured * (uint64_t)n_steps;
+            b->doms[i]->prof.on = prof_on[i];
+        }
+        for (int k = 0; k < n_steps; ++k) MLMD_CUDA(cudaGraphLaunch(exec, cap));
+        MLMD_CUDA(cudaEventRecord(ev_out, cap));
+        MLMD_CUDA(cudaStreamWaitEvent(st, ev_out, 0));
         if (obs_out)
             MLMD_CUDA(cudaMemcpyAsync(obs_out, obs_all, sizeof(double) * 5 * (size_t)nd * n_steps,
                                       cudaMemcpyDeviceToHost, st));
@@ -119,6 +161,9 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         MLMD_CUDA(cudaGetLastError());
         (void)cudaGraphExecDestroy(exec);
         (void)cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        d0.launches += 2ull * (uint64_t)n_steps;
         for (auto* d : b->doms) d->step += n_steps;
         d0.mem.put(A_all);
         d0.mem.put(A_cur);

@@ -54,21 +54,9 @@ __device__ __forceinline__ void st_c(double* p, const Cx<double>& c) {
     *reinterpret_cast<double2*>(p) = make_double2(c.re[0], c.im[0]);
 }
 
-// Geometry and stencil constants of one domain.
-struct Geo {
-    int nx, ny, nz;
-    int ld;        // padded orbitals per row
-    int nv;        // 16-byte vectors per row
-    int64_t ng;
-    double kc0;    // -1/2 * 3 * lap_0 / h^2   (centre weight of the three axes)
-    double kc1;    // -1/2 * lap_1 / h^2
-    double kc2;    // -1/2 * lap_2 / h^2
-    double gk1;    // grad_1 / h
-    double gk2;    // grad_2 / h
-    double dV;
-};
+}  // namespace
 
-Geo make_geo(const Domain& d) {
+Geo geo_of(const Domain& d) {
     Geo G;
     G.nx = d.desc.n[0]; G.ny = d.desc.n[1]; G.nz = d.desc.n[2];
     G.ld = d.ld;
@@ -86,6 +74,10 @@ Geo make_geo(const Domain& d) {
     G.dV = h * h * h;
     return G;
 }
+
+namespace {
+
+Geo make_geo(const Domain& d) { return geo_of(d); }
 
 // Row offsets (in grid points) of the +-1 and +-2 neighbours along one axis
 // with periodic wrap.
@@ -131,62 +123,100 @@ __device__ __forceinline__ void block_sum(double (&v)[W], double* out) {
     }
 }
 
+// Block-wide sum of W values of the working type: warp shuffles in R, then
+// the per-warp partials in FP64; thread 0 writes the totals.
+template <typename R, int W>
+__device__ __forceinline__ void block_sum_r(R (&v)[W], double* out) {
+    __shared__ double sh[32][W];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < W; ++i) sh[warp][i] = (double)v[i];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            double t = lane < nw ? sh[lane][i] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) out[i] = t;
+        }
+    }
+}
+
+// Stencil constants in the working type (computed on the host so that no
+// thread converts from FP64).
+template <typename R> struct GeoR {
+    R kc0, kc1, kc2, gk1, gk2;
+    int nx, ny, nz, ld, nv;
+};
+
+template <typename R>
+GeoR<R> make_geo_r(const Domain& d) {
+    const Geo G = make_geo(d);
+    GeoR<R> g;
+    g.kc0 = (R)G.kc0; g.kc1 = (R)G.kc1; g.kc2 = (R)G.kc2; g.gk1 = (R)G.gk1; g.gk2 = (R)G.gk2;
+    g.nx = G.nx; g.ny = G.ny; g.nz = G.nz; g.ld = G.ld; g.nv = G.nv;
+    return g;
+}
+
 // ---------------------------------------------------------------------------
 // stage: out = psi + gamma * h(A) w
+// Launch: grid (ceil(nx*nv/256), ny, nz), 256 threads; thread t of a block
+// row covers point x = t / nv of line (y, z) and 16-byte vector j = t % nv.
 // ---------------------------------------------------------------------------
 template <typename R, int ORDER, bool NL, bool OBS, bool HAS_PSI>
-__global__ void __launch_bounds__(256) k_stage(Geo G, const R* __restrict__ w, const R* psi, R* out,
-                                               const R* __restrict__ V, const double* __restrict__ f,
+__global__ void __launch_bounds__(256) k_stage(GeoR<R> G, const R* __restrict__ w, const R* psi, R* out,
+                                               const R* __restrict__ V, const R* __restrict__ f,
                                                const double* __restrict__ Ak,
                                                const int32_t* __restrict__ pstart,
                                                const int32_t* __restrict__ patom, const R* __restrict__ pbd,
                                                const R* __restrict__ P, int n_proj, R gre, R gim,
                                                double* __restrict__ obs) {
     constexpr int NC = Vec<R>::NC;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t g = t / G.nv;
-    const int j = (int)(t - g * G.nv);
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (g < G.ng) {
-        const int x = (int)(g % G.nx);
-        const int64_t gyz = g / G.nx;
-        const int y = (int)(gyz % G.ny);
-        const int z = (int)(gyz / G.ny);
+    __shared__ R sA[4];
+    if (threadIdx.x < 3) sA[threadIdx.x] = (R)Ak[threadIdx.x];
+    if (threadIdx.x == 3) sA[3] = (R)(0.5 * (Ak[0] * Ak[0] + Ak[1] * Ak[1] + Ak[2] * Ak[2]));
+    __syncthreads();
+    const unsigned t = blockIdx.x * 256u + threadIdx.x;
+    const int x = (int)(t / (unsigned)G.nv);
+    const int j = (int)(t - (unsigned)x * (unsigned)G.nv);
+    const int y = blockIdx.y, z = blockIdx.z;
+    R acc[5] = {0, 0, 0, 0, 0};
+    if (x < G.nx) {
         const int64_t sy = G.nx, sz = (int64_t)G.nx * G.ny;
-        const Nb bx = nbr(x, G.nx, 1), by = nbr(y, G.ny, sy), bz = nbr(z, G.nz, sz);
-        const R A0 = (R)Ak[0], A1 = (R)Ak[1], A2 = (R)Ak[2];
-        const R diag = V[g] + (R)(0.5 * (Ak[0] * Ak[0] + Ak[1] * Ak[1] + Ak[2] * Ak[2]));
-        const R kc0 = (R)G.kc0, kc1 = (R)G.kc1, kc2 = (R)G.kc2, gk1 = (R)G.gk1, gk2 = (R)G.gk2;
+        const int64_t g = x + sy * y + sz * z;
+        const Nb b[3] = {nbr(x, G.nx, 1), nbr(y, G.ny, sy), nbr(z, G.nz, sz)};
+        const R A0 = sA[0], A1 = sA[1], A2 = sA[2];
+        const R diag = V[g] + sA[3];
 
         const Cx<R> c = ldg_c(rowp(w, g, G.ld, j));
-        Cx<R> lap, d0, d1, d2;
-        {
-            const Nb b[3] = {bx, by, bz};
-            Cx<R>* dd[3] = {&d0, &d1, &d2};
+        Cx<R> lap, dd[3];
 #pragma unroll
-            for (int k = 0; k < NC; ++k) { lap.re[k] = kc0 * c.re[k]; lap.im[k] = kc0 * c.im[k]; }
+        for (int k = 0; k < NC; ++k) { lap.re[k] = G.kc0 * c.re[k]; lap.im[k] = G.kc0 * c.im[k]; }
 #pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                const Cx<R> p1 = ldg_c(rowp(w, g + b[ax].p1, G.ld, j));
-                const Cx<R> m1 = ldg_c(rowp(w, g + b[ax].m1, G.ld, j));
-                Cx<R>& d = *dd[ax];
+        for (int ax = 0; ax < 3; ++ax) {
+            const Cx<R> p1 = ldg_c(rowp(w, g + b[ax].p1, G.ld, j));
+            const Cx<R> m1 = ldg_c(rowp(w, g + b[ax].m1, G.ld, j));
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                lap.re[k] += G.kc1 * (p1.re[k] + m1.re[k]);
+                lap.im[k] += G.kc1 * (p1.im[k] + m1.im[k]);
+                dd[ax].re[k] = G.gk1 * (p1.re[k] - m1.re[k]);
+                dd[ax].im[k] = G.gk1 * (p1.im[k] - m1.im[k]);
+            }
+            if (ORDER == 4) {
+                const Cx<R> p2 = ldg_c(rowp(w, g + b[ax].p2, G.ld, j));
+                const Cx<R> m2 = ldg_c(rowp(w, g + b[ax].m2, G.ld, j));
 #pragma unroll
                 for (int k = 0; k < NC; ++k) {
-                    lap.re[k] += kc1 * (p1.re[k] + m1.re[k]);
-                    lap.im[k] += kc1 * (p1.im[k] + m1.im[k]);
-                    d.re[k] = gk1 * (p1.re[k] - m1.re[k]);
-                    d.im[k] = gk1 * (p1.im[k] - m1.im[k]);
-                }
-                if (ORDER == 4) {
-                    const Cx<R> p2 = ldg_c(rowp(w, g + b[ax].p2, G.ld, j));
-                    const Cx<R> m2 = ldg_c(rowp(w, g + b[ax].m2, G.ld, j));
-#pragma unroll
-                    for (int k = 0; k < NC; ++k) {
-                        lap.re[k] += kc2 * (p2.re[k] + m2.re[k]);
-                        lap.im[k] += kc2 * (p2.im[k] + m2.im[k]);
-                        d.re[k] += gk2 * (p2.re[k] - m2.re[k]);
-                        d.im[k] += gk2 * (p2.im[k] - m2.im[k]);
-                    }
+                    lap.re[k] += G.kc2 * (p2.re[k] + m2.re[k]);
+                    lap.im[k] += G.kc2 * (p2.im[k] + m2.im[k]);
+                    dd[ax].re[k] += G.gk2 * (p2.re[k] - m2.re[k]);
+                    dd[ax].im[k] += G.gk2 * (p2.im[k] - m2.im[k]);
                 }
             }
         }
@@ -194,10 +224,10 @@ __global__ void __launch_bounds__(256) k_stage(Geo G, const R* __restrict__ w, c
         Cx<R> hw;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-            const R gre_ = A0 * d0.re[k] + A1 * d1.re[k] + A2 * d2.re[k];
-            const R gim_ = A0 * d0.im[k] + A1 * d1.im[k] + A2 * d2.im[k];
-            hw.re[k] = lap.re[k] + diag * c.re[k] + gim_;
-            hw.im[k] = lap.im[k] + diag * c.im[k] - gre_;
+            const R gr = A0 * dd[0].re[k] + A1 * dd[1].re[k] + A2 * dd[2].re[k];
+            const R gi = A0 * dd[0].im[k] + A1 * dd[1].im[k] + A2 * dd[2].im[k];
+            hw.re[k] = lap.re[k] + diag * c.re[k] + gi;
+            hw.im[k] = lap.im[k] + diag * c.im[k] - gr;
         }
         if (NL) {
             const int e0 = pstart[g], e1 = pstart[g + 1];
@@ -233,21 +263,24 @@ __global__ void __launch_bounds__(256) k_stage(Geo G, const R* __restrict__ w, c
         if (OBS) {
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
-                const double fo = f[j * NC + k];
-                const double cr = c.re[k], ci = c.im[k];
+                const R fo = f[j * NC + k];
+                const R cr = c.re[k], ci = c.im[k];
                 acc[0] += fo * (cr * cr + ci * ci);
-                acc[1] += fo * (cr * (double)hw.re[k] + ci * (double)hw.im[k]);
-                acc[2] += fo * (cr * (double)d0.im[k] - ci * (double)d0.re[k]);
-                acc[3] += fo * (cr * (double)d1.im[k] - ci * (double)d1.re[k]);
-                acc[4] += fo * (cr * (double)d2.im[k] - ci * (double)d2.re[k]);
+                acc[1] += fo * (cr * hw.re[k] + ci * hw.im[k]);
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) acc[2 + ax] += fo * (cr * dd[ax].im[k] - ci * dd[ax].re[k]);
             }
         }
     }
-    if (OBS) block_sum<5>(acc, obs + (int64_t)blockIdx.x * 5);
+    if (OBS) {
+        const int64_t blin = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+        block_sum_r<R, 5>(acc, obs + blin * 5);
+    }
 }
 
 template <typename R, int ORDER>
-void stage_dispatch(Domain& d, const StageArgs& a, const Geo& G, int blocks) {
+void stage_dispatch(Domain& d, const StageArgs& a, dim3 grid) {
+    const GeoR<R> G = make_geo_r<R>(d);
     const bool nl = d.has_nl() && a.P != nullptr;
     const bool obs = a.obs != nullptr;
     const bool hp = a.psi != nullptr;
@@ -255,11 +288,12 @@ void stage_dispatch(Domain& d, const StageArgs& a, const Geo& G, int blocks) {
     const R* psi = static_cast<const R*>(a.psi);
     R* out = static_cast<R*>(a.out);
     const R* V = static_cast<const R*>(d.V);
+    const R* f = static_cast<const R*>(d.fR);
     const R* pbd = static_cast<const R*>(d.nl.pbd);
     const R* P = static_cast<const R*>(a.P);
 #define MLMD_STAGE(NLv, OBSv, HPv)                                                                   \
-    k_stage<R, ORDER, NLv, OBSv, HPv><<<blocks, 256, 0, d.stream>>>(                                 \
-        G, w, psi, out, V, d.f, a.A, d.nl.pstart, d.nl.patom, pbd, P, d.nl.n_proj, (R)a.gamma_re,   \
+    k_stage<R, ORDER, NLv, OBSv, HPv><<<grid, 256, 0, d.stream>>>(                                   \
+        G, w, psi, out, V, f, a.A, d.nl.pstart, d.nl.patom, pbd, P, d.nl.n_proj, (R)a.gamma_re,     \
         (R)a.gamma_im, a.obs)
     if (nl) {
         if (obs) { if (hp) MLMD_STAGE(true, true, true); else MLMD_STAGE(true, true, false); }
@@ -547,24 +581,30 @@ __global__ void __launch_bounds__(256) k_nl_apply(Geo G, const R* __restrict__ i
 // ---------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------
-int stage_blocks(const Domain& d) {
-    const int64_t nv = d.c64() ? d.ld / 2 : d.ld;
-    return (int)((d.ng * nv + 255) / 256);
+dim3 stage_grid(const Domain& d) {
+    const unsigned nv = d.c64() ? d.ld / 2 : d.ld;
+    return dim3((unsigned)((d.desc.n[0] * nv + 255) / 256), (unsigned)d.desc.n[1], (unsigned)d.desc.n[2]);
 }
 
-void launch_stage(Domain& d, const StageArgs& a) {
-    const Geo G = make_geo(d);
-    const int blocks = stage_blocks(d);
+int stage_blocks(const Domain& d) {
+    const dim3 g = stage_grid(d);
+    return (int)(g.x * g.y * g.z);
+}
+
+int launch_stage(Domain& d, const StageArgs& a, bool* proj_done) {
+    if (launch_stage_tma(d, a, proj_done)) return tma_blocks(d);
+    const dim3 grid = stage_grid(d);
     ProfScope ps(d.prof, MLMD_KERNEL_STAGE, d.stream);
     if (d.c64()) {
-        if (d.desc.fd_order == 4) stage_dispatch<float, 4>(d, a, G, blocks);
-        else stage_dispatch<float, 2>(d, a, G, blocks);
+        if (d.desc.fd_order == 4) stage_dispatch<float, 4>(d, a, grid);
+        else stage_dispatch<float, 2>(d, a, grid);
     } else {
-        if (d.desc.fd_order == 4) stage_dispatch<double, 4>(d, a, G, blocks);
-        else stage_dispatch<double, 2>(d, a, G, blocks);
+        if (d.desc.fd_order == 4) stage_dispatch<double, 4>(d, a, grid);
+        else stage_dispatch<double, 2>(d, a, grid);
     }
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
+    return stage_blocks(d);
 }
 
 void launch_obs_finish(Domain& d, const double* partials, int nblk, const double* A, double* row) {

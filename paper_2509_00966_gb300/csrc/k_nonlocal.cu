@@ -295,7 +295,11 @@ void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj
         if (p) d.mem.put(p);
     nl = Nonlocal{};
     d.Pa = d.Pb = d.Pseg = nullptr;
-    if (n_atoms == 0) return;
+    d.pa_psi = false;
+    if (n_atoms == 0) {
+        tma_build_nl(d, nullptr);
+        return;
+    }
     for (int ax = 0; ax < 3; ++ax)
         MLMD_REQUIRE(d.desc.n[ax] <= kMaxAxis, MLMD_ERR_UNSUPPORTED, "projectors need n <= 1024 per axis");
     const cudaStream_t st = d.stream;
@@ -382,6 +386,7 @@ void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj
     d.mem.put(cnt);
     d.mem.put(cursor);
     d.mem.put(ent_q);
+    tma_build_nl(d, D_host);
 }
 
 void launch_project(Domain& d, const void* w, void* P) {

@@ -1,0 +1,821 @@
+// TMA-staged stage kernel: out = psi + gamma * h(A) w with the Hamiltonian
+// of Eq. 3, 2.5-D blocked, with the nonlocal term of Sec. V.B.5 fused on
+// both sides.
+//
+// A CTA owns an 8 x 8 tile of grid points in x-y, one 128-byte chunk of the
+// orbital row (16 complex64 or 8 complex128 orbitals; 64-byte chunks when the
+// padded row is not a multiple of 128 bytes) and a range of z planes (its
+// "column").  It streams along z: every plane of w is brought into shared
+// memory by five TMA tile loads (the 8 x 8 centre and the four 2-deep
+// star-halo slabs, at periodically wrapped coordinates, so no corner is
+// loaded), through a ring of slots kept ahead of the plane being computed.
+// The x-y neighbours come from shared memory; the z neighbours of each
+// thread's own points stay in registers as the window slides.
+//
+// Nonlocal part: the projections <b|w> of the atoms whose spheres touch the
+// column are staged in shared memory once per CTA (scatter-back B (D o P)),
+// and the projections of the output, <b|out>, are accumulated per column in
+// shared memory and added to the global result with one vector atomic per
+// (atom, projector, 16-byte vector) at the end; the next stage needs no
+// separate projection pass over the state.
+//
+// Every mbarrier wait is bounded: on expiry the CTA raises the domain's
+// error word, waits (bounded) for its copies in flight, and stops.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include "mlmd_internal.cuh"
+
+namespace mlmd {
+
+struct TmaMaps {
+    const void* base = nullptr;
+    CUtensorMap centre{}, xslab{}, yslab{};
+};
+
+struct TmaState {
+    bool ok = false;          // tiles divide the grid and the row splits into chunks
+    int vp = 0;               // 16-byte vectors per point per chunk (8 or 4)
+    int zc = 0;               // planes per CTA
+    int ncols = 0;            // tiles x z-chunks
+    std::vector<TmaMaps> maps;
+    // nonlocal tables of the fused path (device, owned by the domain's allocator)
+    bool nl_ok = false;
+    int maxs = 0;             // most atoms touching one column
+    int32_t* col_start = nullptr;
+    int32_t* col_atom = nullptr;
+    int32_t* ent_slot = nullptr;
+    void* ent_beta = nullptr;
+    void* D = nullptr;
+    int32_t* pe_off = nullptr;
+    int32_t* pe_point = nullptr;
+    void* pe_beta = nullptr;
+};
+
+namespace {
+
+constexpr int TX = 8, TY = 8;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+template <typename R> struct V16;
+template <> struct V16<float> { static constexpr int NC = 2; };
+template <> struct V16<double> { static constexpr int NC = 1; };
+
+template <typename R> struct Cv {
+    R re[V16<R>::NC];
+    R im[V16<R>::NC];
+};
+
+__device__ __forceinline__ void unpack(const float4 t, Cv<float>& c) {
+    c.re[0] = t.x; c.im[0] = t.y; c.re[1] = t.z; c.im[1] = t.w;
+}
+__device__ __forceinline__ void unpack(const float4 t, Cv<double>& c) {
+    double2 d = *reinterpret_cast<const double2*>(&t);
+    c.re[0] = d.x; c.im[0] = d.y;
+}
+__device__ __forceinline__ float4 pack(const Cv<float>& c) { return make_float4(c.re[0], c.im[0], c.re[1], c.im[1]); }
+__device__ __forceinline__ float4 pack(const Cv<double>& c) {
+    double2 d = make_double2(c.re[0], c.im[0]);
+    return *reinterpret_cast<const float4*>(&d);
+}
+
+// ---- PTX wrappers ---------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait on one phase of an mbarrier: false after ~kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+          "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <typename R> struct TGeo {
+    R kc0, kc1, kc2, gk1, gk2;
+    int nx, ny, nz, ld;
+    int ntx;       // tiles along x
+    int zc;        // planes per CTA
+};
+
+// Shared-memory slot: centre [TY][TX][VP], xm/xp [TY][2][VP], ym/yp [2][TX][VP] (16-byte vectors)
+template <int VP> struct Slot {
+    static constexpr int C = 0;
+    static constexpr int XM = C + TY * TX * VP;
+    static constexpr int XP = XM + TY * 2 * VP;
+    static constexpr int YM = XP + TY * 2 * VP;
+    static constexpr int YP = YM + 2 * TX * VP;
+    static constexpr int N = YP + 2 * TX * VP;    // vectors per slot
+    static constexpr uint32_t BYTES = N * 16;
+};
+
+// Vector (x+dx, y+dy) of the plane in slot s, one of dx, dy zero, |d| <= 2.
+template <int VP>
+__device__ __forceinline__ const float4* nb_ptr(const float4* s, int x, int y, int j) {
+    if (x < 0) return s + Slot<VP>::XM + (y * 2 + (x + 2)) * VP + j;
+    if (x >= TX) return s + Slot<VP>::XP + (y * 2 + (x - TX)) * VP + j;
+    if (y < 0) return s + Slot<VP>::YM + ((y + 2) * TX + x) * VP + j;
+    if (y >= TY) return s + Slot<VP>::YP + ((y - TY) * TX + x) * VP + j;
+    return s + Slot<VP>::C + (y * TX + x) * VP + j;
+}
+
+
+// Nonlocal tables of the fused path (see the file comment).
+template <typename R> struct TNl {
+    const int32_t* pstart;     // [N_g + 1] per-point entry ranges
+    const int32_t* slot;       // [n_list] slot of each entry's atom within the point's column
+    const R* beta;             // [n_list][NP] projector values
+    const int32_t* col_start;  // [ncols + 1]
+    const int32_t* col_atom;   // global atom ids of each column, ascending
+    const R* D;                // [n_atoms][NP]
+    const R* Pin;              // <b|w>: [n_atoms][NP] rows of 2 ld reals
+    R* Pout;                   // <b|out> accumulated (zeroed by the caller), or null
+    // projection of the output, plane by plane: entries of (column, plane,
+    // slot) in pe_off[((col * zc + iz) * (maxs + 1)) + s .. + s + 1]
+    const int32_t* pe_off;
+    const int32_t* pe_point;   // local point index (y * 8 + x) within the tile
+    const R* pe_beta;          // [..][NP]
+    R dV;
+    int maxs;                  // staging capacity (atoms per column)
+};
+
+template <typename R, int NP>
+__device__ __forceinline__ void load_beta(const R* p, R (&b)[NP]) {
+    constexpr int PER = 16 / (int)sizeof(R);
+#pragma unroll
+    for (int v = 0; v < NP / PER; ++v) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p) + v);
+        const R* tr = reinterpret_cast<const R*>(&t);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) b[v * PER + k] = tr[k];
+    }
+}
+
+__device__ __forceinline__ void global_add(float* p, float4 v, float s) {
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(s * v.x, s * v.y, s * v.z, s * v.w));
+}
+__device__ __forceinline__ void global_add(double* p, float4 v, double s) {
+    const double2 d = *reinterpret_cast<const double2*>(&v);
+    atomicAdd(p, s * d.x);
+    atomicAdd(p + 1, s * d.y);
+}
+
+template <typename R, int ORDER, int VP, int NP, int NSLOT>
+__global__ void __launch_bounds__(256, 2)
+    k_stage_tma(const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_x,
+                const __grid_constant__ CUtensorMap tm_y, TGeo<R> G, const R* psi, R* out,
+                const R* __restrict__ V, const R* __restrict__ f, const double* __restrict__ Ak, TNl<R> N,
+                R gre, R gim, double* __restrict__ obs, int* err) {
+    constexpr int NC = V16<R>::NC;
+    constexpr int NVT = VP / 4;                     // 16-byte vectors of its point per thread
+    constexpr int OCR = VP * 16 / sizeof(R);        // reals per chunk row
+    constexpr int NPV = (NP > 0 ? NP : 1);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations on a 128-byte boundary (the launch adds 128 bytes of slack)
+    float4* ring = reinterpret_cast<float4*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    float4* sP = ring + NSLOT * Slot<VP>::N;        // [maxs][NP][VP] staged <b|w>
+    float4* sAcc = sP + N.maxs * NPV * VP;          // [maxs][NP][VP] accumulated <b|out>
+    float4* sO = sAcc + N.maxs * NPV * VP;          // [2][64][VP] outputs of the last two planes
+    R* sD = reinterpret_cast<R*>(sO + (NP > 0 ? 2 * 64 * VP : 0));   // [maxs][NP]
+    __shared__ __align__(8) uint64_t bars[NSLOT];
+    __shared__ R sA[4];
+    __shared__ int abort_sh;
+
+    const int tid = threadIdx.x;
+    const int pt = tid >> 2, jv = tid & 3;          // point of the tile, first vector (then jv + 4k)
+    const int lx = pt % TX, ly = pt / TX;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % G.ntx) * TX, y0 = (tile / G.ntx) * TY;
+    const int chunk = blockIdx.y;
+    const int z0 = blockIdx.z * G.zc;
+    const int nzc = min(G.zc, G.nz - z0);           // planes computed by this CTA
+    const int nplanes = nzc + 4;                    // planes z0-2 .. z0+nzc+1
+    const int c0 = chunk * OCR;                     // first real of the chunk within a row
+    const bool has_psi = psi != nullptr;
+    const bool do_obs = obs != nullptr;
+    const bool proj = NP > 0 && N.Pout != nullptr;
+    const int col = blockIdx.x + gridDim.x * blockIdx.z;
+
+    if (tid == 0) {
+        for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
+        abort_sh = 0;
+        fence_proxy_async();
+    }
+    if (tid < 3) sA[tid] = (R)Ak[tid];
+    if (tid == 3) sA[3] = (R)(0.5 * (Ak[0] * Ak[0] + Ak[1] * Ak[1] + Ak[2] * Ak[2]));
+    int cs = 0, na = 0;
+    if (NP > 0) {
+        cs = N.col_start[col];
+        na = N.col_start[col + 1] - cs;
+        for (int idx = tid; idx < na * NPV * VP; idx += 256) {
+            const int s = idx / (NPV * VP), r = idx - s * (NPV * VP), i = r / VP, jj = r - i * VP;
+            const int64_t a = N.col_atom[cs + s];
+            sP[idx] = __ldg(reinterpret_cast<const float4*>(N.Pin + (a * NPV + i) * 2 * G.ld + c0) + jj);
+            sAcc[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int idx = tid; idx < na * NPV; idx += 256) {
+            const int s = idx / NPV, i = idx - s * NPV;
+            sD[idx] = N.D[(int64_t)N.col_atom[cs + s] * NPV + i];
+        }
+    }
+    __syncthreads();
+
+    auto issue = [&](int p) {   // TMA of plane p (z = z0 - 2 + p) into slot p % NSLOT
+        const int s = p % NSLOT;
+        const int zz = ((z0 - 2 + p) % G.nz + G.nz) % G.nz;
+        float4* d = ring + s * Slot<VP>::N;
+        uint64_t* b = &bars[s];
+        mbar_expect_tx(b, Slot<VP>::BYTES);
+        tma_load_4d(d + Slot<VP>::C, &tm_c, c0, x0, y0, zz, b);
+        tma_load_4d(d + Slot<VP>::XM, &tm_x, c0, (x0 - 2 + G.nx) % G.nx, y0, zz, b);
+        tma_load_4d(d + Slot<VP>::XP, &tm_x, c0, (x0 + TX) % G.nx, y0, zz, b);
+        tma_load_4d(d + Slot<VP>::YM, &tm_y, c0, x0, (y0 - 2 + G.ny) % G.ny, zz, b);
+        tma_load_4d(d + Slot<VP>::YP, &tm_y, c0, x0, (y0 + TY) % G.ny, zz, b);
+    };
+    auto wait_plane = [&](int p) -> bool { return mbar_wait_bounded(&bars[p % NSLOT], (uint32_t)((p / NSLOT) & 1)); };
+
+    // shared-memory offsets (16-byte vectors) of this thread's first vector and
+    // of its x-y neighbours within a slot; vector k adds 4 k
+    const int offC = Slot<VP>::C + (ly * TX + lx) * VP + jv;
+    int offN[8];
+    {
+        const int dx[8] = {1, -1, 0, 0, 2, -2, 0, 0}, dy[8] = {0, 0, 1, -1, 0, 0, 2, -2};
+#pragma unroll
+        for (int n = 0; n < 8; ++n) offN[n] = (int)(nb_ptr<VP>(ring, lx + dx[n], ly + dy[n], jv) - ring);
+    }
+
+    int issued = 0, waited = 0;                     // meaningful in thread 0
+    if (tid == 0) {
+        for (int p = 0; p < NSLOT && p < nplanes; ++p) issue(p);
+        issued = min(NSLOT, nplanes);
+    }
+    // register window of the thread's vectors: q[k][0..4] = planes z-2 .. z+2
+    Cv<R> q[NVT][5];
+    bool ok = true;
+    for (int p = 0; p < 4; ++p) ok = ok && wait_plane(p);
+    if (!ok) abort_sh = 1;
+    __syncthreads();
+    const bool aborted0 = abort_sh != 0;
+    if (!aborted0) {
+        for (int p = 0; p < 4; ++p) {
+            const float4* s = ring + (p % NSLOT) * Slot<VP>::N;
+#pragma unroll
+            for (int k = 0; k < NVT; ++k) unpack(s[offC + 4 * k], q[k][p]);
+        }
+    }
+    if (tid == 0) waited = aborted0 ? 0 : 4;
+    __syncthreads();
+    if (tid == 0 && !aborted0 && issued < nplanes) {   // slot 0 (plane z0-2) is free again
+        fence_proxy_async();
+        issue(issued);
+        ++issued;
+    }
+
+    // <b|out> of plane iz (outputs in sO[iz & 1]).  Warp w owns the atom
+    // slots s = w, w + 8, ...; its lanes split the 16-byte vectors (VP of
+    // them) and the slot's entries (32 / VP groups), reduce across the entry
+    // groups with shuffles, and one group updates the warp-owned
+    // accumulators, so no two warps touch the same accumulator.
+    auto project_plane = [&](int iz) {
+        constexpr int NEG = 32 / VP;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int jj = lane % VP, eg = lane / VP;
+        const float4* so = sO + (iz & 1) * 64 * VP;
+        const int32_t* po = N.pe_off + ((int64_t)col * G.zc + iz) * (N.maxs + 1);
+        for (int s = warp; s < na; s += 8) {
+            const int e0 = po[s], e1 = po[s + 1];
+            Cv<R> a[NPV];
+#pragma unroll
+            for (int pi = 0; pi < NPV; ++pi)
+#pragma unroll
+                for (int u = 0; u < NC; ++u) { a[pi].re[u] = 0; a[pi].im[u] = 0; }
+            for (int e = e0 + eg; e < e1; e += NEG) {
+                R b[NPV];
+                load_beta<R, NPV>(N.pe_beta + (int64_t)e * NPV, b);
+                Cv<R> ov;
+                unpack(so[N.pe_point[e] * VP + jj], ov);
+#pragma unroll
+                for (int pi = 0; pi < NPV; ++pi)
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) {
+                        a[pi].re[u] += b[pi] * ov.re[u];
+                        a[pi].im[u] += b[pi] * ov.im[u];
+                    }
+            }
+#pragma unroll
+            for (int off = VP; off < 32; off <<= 1)
+#pragma unroll
+                for (int pi = 0; pi < NPV; ++pi)
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) {
+                        a[pi].re[u] += __shfl_xor_sync(0xffffffffu, a[pi].re[u], off);
+                        a[pi].im[u] += __shfl_xor_sync(0xffffffffu, a[pi].im[u], off);
+                    }
+            if (eg == 0) {
+#pragma unroll
+                for (int pi = 0; pi < NPV; ++pi) {
+                    float4* dst = &sAcc[(s * NPV + pi) * VP + jj];
+                    Cv<R> av;
+                    unpack(*dst, av);
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) { av.re[u] += a[pi].re[u]; av.im[u] += a[pi].im[u]; }
+                    *dst = pack(av);
+                }
+            }
+        }
+    };
+
+    R acc[5] = {0, 0, 0, 0, 0};
+    const int64_t plane_stride = (int64_t)G.nx * G.ny;
+    int64_t g = (x0 + lx) + (int64_t)G.nx * (y0 + ly) + plane_stride * z0;
+    const int64_t row = 2 * (int64_t)G.ld;
+    for (int i = 0; i < nzc && !aborted0; ++i, g += plane_stride) {
+        // per-point global loads first, so that they overlap the plane wait
+        // and the shared-memory stencil
+        const R vv = V[g];
+        float4 pp[NVT];
+        if (has_psi)
+#pragma unroll
+            for (int k = 0; k < NVT; ++k) pp[k] = *(reinterpret_cast<const float4*>(psi + g * row + c0) + jv + 4 * k);
+        int e0 = 0, e1 = 0;
+        if (NP > 0) { e0 = N.pstart[g]; e1 = N.pstart[g + 1]; }
+        // plane z+2 (p = i+4) must have landed
+        ok = wait_plane(i + 4);
+        if (!ok) abort_sh = 1;
+        __syncthreads();                    // also: all reads of the slot of plane z-1 are done
+        if (abort_sh) break;
+        if (tid == 0) {
+            waited = i + 5;
+            if (issued < nplanes) {         // next plane into the slot of plane z-1
+                fence_proxy_async();
+                issue(issued);
+                ++issued;
+            }
+        }
+        if (proj && i > 0) project_plane(i - 1);   // its outputs were written before barrier A
+        const float4* sc = ring + ((i + 2) % NSLOT) * Slot<VP>::N;    // plane z
+        const float4* s4 = ring + ((i + 4) % NSLOT) * Slot<VP>::N;    // plane z+2
+        Cv<R> hw[NVT], dd[NVT][3];
+#pragma unroll
+        for (int k = 0; k < NVT; ++k) {
+            unpack(s4[offC + 4 * k], q[k][4]);
+            const Cv<R>& c = q[k][2];
+            Cv<R> lap, t1, t2, t3, t4;
+#pragma unroll
+            for (int e = 0; e < NC; ++e) { lap.re[e] = G.kc0 * c.re[e]; lap.im[e] = G.kc0 * c.im[e]; }
+#pragma unroll
+            for (int ax = 0; ax < 2; ++ax) {
+                unpack(sc[offN[2 * ax] + 4 * k], t1);
+                unpack(sc[offN[2 * ax + 1] + 4 * k], t2);
+                if (ORDER == 4) {
+                    unpack(sc[offN[4 + 2 * ax] + 4 * k], t3);
+                    unpack(sc[offN[5 + 2 * ax] + 4 * k], t4);
+                }
+#pragma unroll
+                for (int e = 0; e < NC; ++e) {
+                    lap.re[e] += G.kc1 * (t1.re[e] + t2.re[e]);
+                    lap.im[e] += G.kc1 * (t1.im[e] + t2.im[e]);
+                    dd[k][ax].re[e] = G.gk1 * (t1.re[e] - t2.re[e]);
+                    dd[k][ax].im[e] = G.gk1 * (t1.im[e] - t2.im[e]);
+                    if (ORDER == 4) {
+                        lap.re[e] += G.kc2 * (t3.re[e] + t4.re[e]);
+                        lap.im[e] += G.kc2 * (t3.im[e] + t4.im[e]);
+                        dd[k][ax].re[e] += G.gk2 * (t3.re[e] - t4.re[e]);
+                        dd[k][ax].im[e] += G.gk2 * (t3.im[e] - t4.im[e]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < NC; ++e) {
+                lap.re[e] += G.kc1 * (q[k][3].re[e] + q[k][1].re[e]);
+                lap.im[e] += G.kc1 * (q[k][3].im[e] + q[k][1].im[e]);
+                dd[k][2].re[e] = G.gk1 * (q[k][3].re[e] - q[k][1].re[e]);
+                dd[k][2].im[e] = G.gk1 * (q[k][3].im[e] - q[k][1].im[e]);
+                if (ORDER == 4) {
+                    lap.re[e] += G.kc2 * (q[k][4].re[e] + q[k][0].re[e]);
+                    lap.im[e] += G.kc2 * (q[k][4].im[e] + q[k][0].im[e]);
+                    dd[k][2].re[e] += G.gk2 * (q[k][4].re[e] - q[k][0].re[e]);
+                    dd[k][2].im[e] += G.gk2 * (q[k][4].im[e] - q[k][0].im[e]);
+                }
+            }
+            const R diag = vv + sA[3];
+#pragma unroll
+            for (int e = 0; e < NC; ++e) {
+                const R gr = sA[0] * dd[k][0].re[e] + sA[1] * dd[k][1].re[e] + sA[2] * dd[k][2].re[e];
+                const R gi = sA[0] * dd[k][0].im[e] + sA[1] * dd[k][1].im[e] + sA[2] * dd[k][2].im[e];
+                hw[k].re[e] = lap.re[e] + diag * c.re[e] + gi;
+                hw[k].im[e] = lap.im[e] + diag * c.im[e] - gr;
+            }
+        }
+        if (NP > 0) {           // scatter-back: sum_(a,i) b_ai(r) D_ai <b_ai|w>
+            for (int e = e0; e < e1; ++e) {
+                const int s = N.slot[e];
+                R b[NPV];
+                load_beta<R, NPV>(N.beta + (int64_t)e * NPV, b);
+#pragma unroll
+                for (int pi = 0; pi < NPV; ++pi) {
+                    const R bd = b[pi] * sD[s * NPV + pi];
+#pragma unroll
+                    for (int k = 0; k < NVT; ++k) {
+                        Cv<R> pv;
+                        unpack(sP[(s * NPV + pi) * VP + jv + 4 * k], pv);
+#pragma unroll
+                        for (int u = 0; u < NC; ++u) {
+                            hw[k].re[u] += bd * pv.re[u];
+                            hw[k].im[u] += bd * pv.im[u];
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NVT; ++k) {
+            Cv<R> o;
+            if (has_psi) {
+                Cv<R> ps;
+                unpack(pp[k], ps);
+#pragma unroll
+                for (int e = 0; e < NC; ++e) {
+                    o.re[e] = ps.re[e] + gre * hw[k].re[e] - gim * hw[k].im[e];
+                    o.im[e] = ps.im[e] + gre * hw[k].im[e] + gim * hw[k].re[e];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < NC; ++e) {
+                    o.re[e] = gre * hw[k].re[e] - gim * hw[k].im[e];
+                    o.im[e] = gre * hw[k].im[e] + gim * hw[k].re[e];
+                }
+            }
+            const float4 ov = pack(o);
+            *(reinterpret_cast<float4*>(out + g * row + c0) + jv + 4 * k) = ov;
+            if (proj) sO[(i & 1) * 64 * VP + pt * VP + jv + 4 * k] = ov;
+            if (do_obs) {
+                const Cv<R>& c = q[k][2];
+#pragma unroll
+                for (int e = 0; e < NC; ++e) {
+                    const R fo = f[c0 / 2 + (jv + 4 * k) * NC + e];
+                    const R cr = c.re[e], ci = c.im[e];
+                    acc[0] += fo * (cr * cr + ci * ci);
+                    acc[1] += fo * (cr * hw[k].re[e] + ci * hw[k].im[e]);
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) acc[2 + ax] += fo * (cr * dd[k][ax].im[e] - ci * dd[k][ax].re[e]);
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) q[k][w] = q[k][w + 1];
+        }
+    }
+    if (abort_sh) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // let the copies still in flight land before the CTA's shared memory goes away
+            for (int p = waited; p < issued; ++p) (void)wait_plane(p);
+        }
+    }
+    if (proj) {
+        __syncthreads();
+        if (!abort_sh && nzc > 0) project_plane(nzc - 1);
+        __syncthreads();
+        if (!abort_sh)
+            for (int idx = tid; idx < na * NPV * VP; idx += 256) {
+                const int s = idx / (NPV * VP), r = idx - s * (NPV * VP), i = r / VP, jj = r - i * VP;
+                const int64_t a = N.col_atom[cs + s];
+                global_add(N.Pout + (a * NPV + i) * 2 * G.ld + c0 + jj * (16 / (int)sizeof(R)), sAcc[idx], N.dV);
+            }
+    }
+    if (do_obs) {
+        __shared__ double sh[8][5];
+        const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+            for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+        if (lane == 0)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sh[warp][v] = (double)acc[v];
+        __syncthreads();
+        if (tid < 5) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += sh[w][tid];
+            const int64_t blin = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+            obs[blin * 5 + tid] = t;
+        }
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <int NP> struct SlotsFor { static constexpr int value = 4; };
+
+template <typename R, int VP, int NP>
+size_t smem_bytes(int maxs) {
+    constexpr int NSLOT = SlotsFor<NP>::value;
+    const int npv = NP > 0 ? NP : 1;
+    size_t b = (size_t)NSLOT * Slot<VP>::BYTES;
+    if (NP > 0)
+        b += 2 * (size_t)maxs * npv * VP * 16 + 2 * 64 * VP * 16 + ((size_t)maxs * npv * sizeof(R) + 15) / 16 * 16;
+    return b + 128;
+}
+
+template <typename R, int ORDER, int VP, int NP>
+void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool proj) {
+    constexpr int NSLOT = SlotsFor<NP>::value;
+    const TmaState& t = *d.tma;
+    const Geo G0 = geo_of(d);
+    TGeo<R> G;
+    G.kc0 = (R)G0.kc0; G.kc1 = (R)G0.kc1; G.kc2 = (R)G0.kc2; G.gk1 = (R)G0.gk1; G.gk2 = (R)G0.gk2;
+    G.nx = d.desc.n[0]; G.ny = d.desc.n[1]; G.nz = d.desc.n[2]; G.ld = d.ld;
+    G.ntx = d.desc.n[0] / TX;
+    G.zc = t.zc;
+    TNl<R> N{};
+    if (NP > 0) {
+        N.pstart = d.nl.pstart;
+        N.slot = t.ent_slot;
+        N.beta = static_cast<const R*>(t.ent_beta);
+        N.col_start = t.col_start;
+        N.col_atom = t.col_atom;
+        N.D = static_cast<const R*>(t.D);
+        N.Pin = static_cast<const R*>(a.P);
+        N.Pout = proj ? static_cast<R*>(a.P_out) : nullptr;
+        N.pe_off = t.pe_off;
+        N.pe_point = t.pe_point;
+        N.pe_beta = static_cast<const R*>(t.pe_beta);
+        N.dV = (R)(d.desc.h * d.desc.h * d.desc.h);
+        N.maxs = t.maxs;
+    }
+    const size_t smem = smem_bytes<R, VP, NP>(NP > 0 ? t.maxs : 0);
+    auto kern = k_stage_tma<R, ORDER, VP, NP, NSLOT>;
+    static size_t attr_bytes = 0;
+    if (smem > attr_bytes) {
+        MLMD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_bytes = smem;
+    }
+    kern<<<grid, 256, smem, d.stream>>>(m.centre, m.xslab, m.yslab, G, static_cast<const R*>(a.psi),
+                                       static_cast<R*>(a.out), static_cast<const R*>(d.V),
+                                       static_cast<const R*>(d.fR), a.A, N, (R)a.gamma_re, (R)a.gamma_im, a.obs,
+                                       d.err_flag);
+}
+
+template <typename R, int VP, int NP>
+void tma_order(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool proj) {
+    if (d.desc.fd_order == 4) tma_launch<R, 4, VP, NP>(d, a, m, grid, proj);
+    else tma_launch<R, 2, VP, NP>(d, a, m, grid, proj);
+}
+
+template <typename R, int VP>
+void tma_np(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool nl, bool proj) {
+    if (!nl) tma_order<R, VP, 0>(d, a, m, grid, false);
+    else if (d.nl.n_proj == 4) tma_order<R, VP, 4>(d, a, m, grid, proj);
+    else tma_order<R, VP, 8>(d, a, m, grid, proj);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        MLMD_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        MLMD_REQUIRE(q == cudaDriverEntryPointSuccess && p, MLMD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+void encode(CUtensorMap* map, const Domain& d, const void* base, uint32_t bx, uint32_t by) {
+    const size_t rs = d.c64() ? sizeof(float) : sizeof(double);
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * d.ld, (cuuint64_t)d.desc.n[0], (cuuint64_t)d.desc.n[1],
+                                (cuuint64_t)d.desc.n[2]};
+    const cuuint64_t row = (cuuint64_t)2 * d.ld * rs;
+    const cuuint64_t strides[3] = {row, row * d.desc.n[0], row * d.desc.n[0] * d.desc.n[1]};
+    const cuuint32_t box[4] = {(cuuint32_t)(d.tma->vp * 16 / rs), bx, by, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode_fn()(map, d.c64() ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    MLMD_REQUIRE(r == CUDA_SUCCESS, MLMD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+}
+
+TmaMaps maps_for(Domain& d, const void* base) {
+    for (const auto& m : d.tma->maps)
+        if (m.base == base) return m;
+    if (d.tma->maps.size() >= 64) d.tma->maps.clear();
+    TmaMaps m;
+    m.base = base;
+    encode(&m.centre, d, base, TX, TY);
+    encode(&m.xslab, d, base, 2, TY);
+    encode(&m.yslab, d, base, TX, 2);
+    d.tma->maps.push_back(m);
+    return m;
+}
+
+int chunks_of(const Domain& d) { return (int)((size_t)d.ld * d.elem / (d.tma->vp * 16)); }
+
+}  // namespace
+
+void tma_setup(Domain& d) {
+    if (!d.tma) d.tma = new TmaState();
+    TmaState& t = *d.tma;
+    t.maps.clear();
+    const int nx = d.desc.n[0], ny = d.desc.n[1], nz = d.desc.n[2];
+    const size_t row_bytes = (size_t)d.ld * d.elem;
+    t.vp = (row_bytes % 128 == 0) ? 8 : ((row_bytes % 64 == 0 && d.c64()) ? 4 : 0);
+    t.ok = t.vp != 0 && nx % TX == 0 && ny % TY == 0 && std::getenv("MLMD_NO_TMA") == nullptr;
+    if (!t.ok) return;
+    const int base = (nx / TX) * (ny / TY) * chunks_of(d);
+    const int nzch = std::max(1, std::min((608 + base - 1) / base, std::max(1, nz / 4)));
+    t.zc = (nz + nzch - 1) / nzch;
+    t.ncols = (nx / TX) * (ny / TY) * ((nz + t.zc - 1) / t.zc);
+}
+
+void tma_release(Domain& d) {
+    delete d.tma;
+    d.tma = nullptr;
+}
+
+// Per-column tables of the fused nonlocal path, built on the host from the
+// device lists (set-up, not on the time-step path).
+void tma_build_nl(Domain& d, const double* D_host) {
+    if (!d.tma || !d.tma->ok) return;
+    TmaState& t = *d.tma;
+    for (void* p : {(void*)t.col_start, (void*)t.col_atom, (void*)t.ent_slot, t.ent_beta, t.D, (void*)t.pe_off,
+                    (void*)t.pe_point, t.pe_beta})
+        if (p) d.mem.put(p);
+    t.col_start = t.col_atom = t.ent_slot = t.pe_off = t.pe_point = nullptr;
+    t.ent_beta = t.D = t.pe_beta = nullptr;
+    t.nl_ok = false;
+    t.maxs = 0;
+    const Nonlocal& nl = d.nl;
+    if (nl.n_atoms == 0 || nl.n_list == 0) return;
+    const int nx = d.desc.n[0], ny = d.desc.n[1];
+    const int ntx = nx / TX, ntiles = ntx * (ny / TY);
+    const int np = nl.n_proj;
+    std::vector<int32_t> idx(nl.n_list), pstart_dev(d.ng + 1);
+    std::vector<double> beta((size_t)nl.n_list * np);
+    MLMD_CUDA(cudaMemcpyAsync(idx.data(), nl.idx, sizeof(int32_t) * nl.n_list, cudaMemcpyDeviceToHost, d.stream));
+    MLMD_CUDA(cudaMemcpyAsync(beta.data(), nl.beta64, sizeof(double) * beta.size(), cudaMemcpyDeviceToHost, d.stream));
+    MLMD_CUDA(cudaMemcpyAsync(pstart_dev.data(), nl.pstart, sizeof(int32_t) * (d.ng + 1), cudaMemcpyDeviceToHost,
+                              d.stream));
+    MLMD_CUDA(cudaStreamSynchronize(d.stream));
+    auto col_of = [&](int64_t g) {
+        const int x = (int)(g % nx), y = (int)((g / nx) % ny), z = (int)(g / ((int64_t)nx * ny));
+        return (x / TX + ntx * (y / TY)) + ntiles * (z / t.zc);
+    };
+    std::vector<std::vector<int32_t>> catoms(t.ncols);
+    std::vector<int32_t> last(t.ncols, -1);
+    std::vector<int32_t> qslot(nl.n_list);
+    std::vector<int32_t> pcount(d.ng, 0);
+    for (int a = 0; a < nl.n_atoms; ++a)
+        for (int64_t q = nl.h_off[a]; q < nl.h_off[a + 1]; ++q) {
+            const int c = col_of(idx[q]);
+            if (last[c] != a) { catoms[c].push_back(a); last[c] = a; }
+            qslot[q] = (int32_t)catoms[c].size() - 1;
+            pcount[idx[q]]++;
+        }
+    std::vector<int32_t> pstart(d.ng + 1, 0), cur(d.ng, 0);
+    for (int64_t g = 0; g < d.ng; ++g) pstart[g + 1] = pstart[g] + pcount[g];
+    MLMD_REQUIRE(pstart == pstart_dev, MLMD_ERR_STATE, "per-point projector ranges disagree");
+    const size_t rs = d.c64() ? sizeof(float) : sizeof(double);
+    std::vector<int32_t> ent_slot(nl.n_list);
+    std::vector<unsigned char> ent_beta((size_t)nl.n_list * np * rs);
+    for (int a = 0; a < nl.n_atoms; ++a)
+        for (int64_t q = nl.h_off[a]; q < nl.h_off[a + 1]; ++q) {
+            const int64_t g = idx[q];
+            const int64_t e = pstart[g] + cur[g]++;
+            ent_slot[e] = qslot[q];
+            for (int i = 0; i < np; ++i) {
+                if (rs == 4) reinterpret_cast<float*>(ent_beta.data())[e * np + i] = (float)beta[q * np + i];
+                else reinterpret_cast<double*>(ent_beta.data())[e * np + i] = beta[q * np + i];
+            }
+        }
+    std::vector<int32_t> col_start(t.ncols + 1, 0), col_atom;
+    for (int c = 0; c < t.ncols; ++c) {
+        col_start[c + 1] = col_start[c] + (int32_t)catoms[c].size();
+        t.maxs = std::max<int>(t.maxs, (int)catoms[c].size());
+        col_atom.insert(col_atom.end(), catoms[c].begin(), catoms[c].end());
+    }
+    std::vector<unsigned char> Dr((size_t)nl.n_atoms * np * rs);
+    for (int64_t k = 0; k < (int64_t)nl.n_atoms * np; ++k) {
+        if (rs == 4) reinterpret_cast<float*>(Dr.data())[k] = (float)D_host[k];
+        else reinterpret_cast<double*>(Dr.data())[k] = D_host[k];
+    }
+    // per (column, plane, slot) lists of (point, beta) for the output projection
+    const int M = std::max(t.maxs, 1);
+    const int64_t ngrp = (int64_t)t.ncols * t.zc;
+    std::vector<int32_t> pcnt((size_t)ngrp * M + 1, 0);
+    auto key_of = [&](int64_t g, int slot) {
+        const int z = (int)(g / ((int64_t)nx * ny));
+        return ((int64_t)col_of(g) * t.zc + (z % t.zc)) * M + slot;
+    };
+    for (int64_t q = 0; q < nl.n_list; ++q) pcnt[key_of(idx[q], qslot[q])]++;
+    std::vector<int32_t> pst((size_t)ngrp * M + 1, 0);
+    for (size_t k = 0; k + 1 < pst.size(); ++k) pst[k + 1] = pst[k] + pcnt[k];
+    std::vector<int32_t> pe_off((size_t)ngrp * (M + 1));
+    for (int64_t gr = 0; gr < ngrp; ++gr)
+        for (int s2 = 0; s2 <= M; ++s2) pe_off[gr * (M + 1) + s2] = pst[gr * M + s2];
+    std::vector<int32_t> pe_point(nl.n_list), pcur((size_t)ngrp * M, 0);
+    std::vector<unsigned char> pe_beta((size_t)nl.n_list * np * rs);
+    for (int a = 0; a < nl.n_atoms; ++a)
+        for (int64_t q = nl.h_off[a]; q < nl.h_off[a + 1]; ++q) {
+            const int64_t g = idx[q];
+            const int64_t k = key_of(g, qslot[q]);
+            const int64_t e = pst[k] + pcur[k]++;
+            pe_point[e] = (int32_t)((((g / nx) % ny) % TY) * TX + (g % nx) % TX);
+            for (int i = 0; i < np; ++i) {
+                if (rs == 4) reinterpret_cast<float*>(pe_beta.data())[e * np + i] = (float)beta[q * np + i];
+                else reinterpret_cast<double*>(pe_beta.data())[e * np + i] = beta[q * np + i];
+            }
+        }
+    size_t sm;
+    if (d.c64()) sm = (t.vp == 8) ? (np == 4 ? smem_bytes<float, 8, 4>(t.maxs) : smem_bytes<float, 8, 8>(t.maxs))
+                                  : (np == 4 ? smem_bytes<float, 4, 4>(t.maxs) : smem_bytes<float, 4, 8>(t.maxs));
+    else sm = np == 4 ? smem_bytes<double, 8, 4>(t.maxs) : smem_bytes<double, 8, 8>(t.maxs);
+    if (sm > 200 * 1024) return;   // too many atoms per column for the staging: plain kernel
+    t.col_start = (int32_t*)d.mem.get(sizeof(int32_t) * col_start.size());
+    t.col_atom = (int32_t*)d.mem.get(sizeof(int32_t) * std::max<size_t>(col_atom.size(), 1));
+    t.ent_slot = (int32_t*)d.mem.get(sizeof(int32_t) * ent_slot.size());
+    t.ent_beta = d.mem.get(ent_beta.size());
+    t.D = d.mem.get(Dr.size());
+    MLMD_CUDA(cudaMemcpyAsync(t.col_start, col_start.data(), sizeof(int32_t) * col_start.size(), cudaMemcpyHostToDevice, d.stream));
+    if (!col_atom.empty())
+        MLMD_CUDA(cudaMemcpyAsync(t.col_atom, col_atom.data(), sizeof(int32_t) * col_atom.size(), cudaMemcpyHostToDevice, d.stream));
+    MLMD_CUDA(cudaMemcpyAsync(t.ent_slot, ent_slot.data(), sizeof(int32_t) * ent_slot.size(), cudaMemcpyHostToDevice, d.stream));
+    MLMD_CUDA(cudaMemcpyAsync(t.ent_beta, ent_beta.data(), ent_beta.size(), cudaMemcpyHostToDevice, d.stream));
+    MLMD_CUDA(cudaMemcpyAsync(t.D, Dr.data(), Dr.size(), cudaMemcpyHostToDevice, d.stream));
+    t.pe_off = (int32_t*)d.mem.get(sizeof(int32_t) * pe_off.size());
+    t.pe_point = (int32_t*)d.mem.get(sizeof(int32_t) * pe_point.size());
+    t.pe_beta = d.mem.get(pe_beta.size());
+    MLMD_CUDA(cudaMemcpyAsync(t.pe_off, pe_off.data(), sizeof(int32_t) * pe_off.size(), cudaMemcpyHostToDevice, d.stream));
+    MLMD_CUDA(cudaMemcpyAsync(t.pe_point, pe_point.data(), sizeof(int32_t) * pe_point.size(), cudaMemcpyHostToDevice, d.stream));
+    MLMD_CUDA(cudaMemcpyAsync(t.pe_beta, pe_beta.data(), pe_beta.size(), cudaMemcpyHostToDevice, d.stream));
+    MLMD_CUDA(cudaStreamSynchronize(d.stream));
+    t.nl_ok = true;
+}
+
+bool tma_fused_nl(const Domain& d) { return d.tma && d.tma->ok && d.has_nl() && d.tma->nl_ok; }
+
+int tma_blocks(const Domain& d) {
+    if (!d.tma || !d.tma->ok) return 0;
+    return (d.desc.n[0] / TX) * (d.desc.n[1] / TY) * chunks_of(d) * ((d.desc.n[2] + d.tma->zc - 1) / d.tma->zc);
+}
+
+bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done) {
+    if (proj_done) *proj_done = false;
+    if (!d.tma || !d.tma->ok) return false;
+    const bool nl = d.has_nl() && a.P != nullptr;
+    if (nl && !d.tma->nl_ok) return false;
+    const bool proj = nl && a.P_out != nullptr;
+    const TmaState& t = *d.tma;
+    const TmaMaps m = maps_for(d, a.w);
+    dim3 grid((d.desc.n[0] / TX) * (d.desc.n[1] / TY), chunks_of(d), (d.desc.n[2] + t.zc - 1) / t.zc);
+    if (proj)
+        MLMD_CUDA(cudaMemsetAsync(a.P_out, 0, (size_t)d.nl.n_atoms * d.nl.n_proj * d.ld * d.elem, d.stream));
+    ProfScope ps(d.prof, MLMD_KERNEL_STAGE, d.stream);
+    if (d.c64()) {
+        if (t.vp == 8) tma_np<float, 8>(d, a, m, grid, nl, proj);
+        else tma_np<float, 4>(d, a, m, grid, nl, proj);
+    } else {
+        tma_np<double, 8>(d, a, m, grid, nl, proj);
+    }
+    d.launches++;
+    MLMD_CUDA(cudaGetLastError());
+    if (proj_done) *proj_done = proj;
+    return true;
+}
+
+}  // namespace mlmd

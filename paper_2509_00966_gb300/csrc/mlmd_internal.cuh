@@ -50,6 +50,22 @@ struct Alloc {
     void release_all();
 };
 
+// Stencil geometry of one domain (FP64; kernels convert once on the host).
+struct Geo {
+    int nx, ny, nz;
+    int ld;        // padded orbitals per row
+    int nv;        // 16-byte vectors per row
+    int64_t ng;
+    double kc0;    // -1/2 * 3 * lap_0 / h^2   (centre weight of the three axes)
+    double kc1;    // -1/2 * lap_1 / h^2
+    double kc2;    // -1/2 * lap_2 / h^2
+    double gk1;    // grad_1 / h
+    double gk2;    // grad_2 / h
+    double dV;
+};
+
+struct TmaState;   // TMA stage-kernel state (tensor maps, tiling), k_stage_tma.cu
+
 // Projector tables built on the device by set_projectors.
 struct Nonlocal {
     int n_atoms = 0;
@@ -112,6 +128,7 @@ struct Domain {
     void* V = nullptr;             // [ng] local potential (working real type)
     double* V64 = nullptr;         // [ng] FP64 copy (adjoint, batch)
     double* f = nullptr;           // [ld] occupations, zero on padding
+    void* fR = nullptr;            // [ld] occupations in the working real type
     Nonlocal nl;
     void* Pa = nullptr;            // projections [n_atoms][n_proj][ld] complex
     void* Pb = nullptr;
@@ -126,9 +143,12 @@ struct Domain {
     size_t dense_bytes = 0;
 
     int64_t step = 0;              // steps since set_orbitals
+    bool pa_psi = false;           // Pa holds <b|psi> of the current orbitals
     bool psi0_valid = false;
     uint64_t launches = 0;
     Profiler prof;
+    TmaState* tma = nullptr;
+    int* err_flag = nullptr;       // device word raised by a kernel whose bounded wait expired
     mlmd_status latched = MLMD_OK;
     std::string err;
 
@@ -145,16 +165,32 @@ struct Domain {
 // projectors).  When obs != null, also writes per-block partial observables
 // of w (which must then equal psi's state) into obs.
 struct StageArgs {
-    const void* w;
-    const void* psi;
-    void* out;
-    const void* P;
-    const double* A;               // device [3]
-    double gamma_re, gamma_im;
-    double* obs;                   // per-block partials [blocks][5] or null
+    const void* w = nullptr;
+    const void* psi = nullptr;
+    void* out = nullptr;
+    const void* P = nullptr;       // <b|w> for the scatter-back
+    void* P_out = nullptr;         // if set: <b|out> wanted (the TMA path fuses it)
+    const double* A = nullptr;     // device [3]
+    double gamma_re = 0.0, gamma_im = 0.0;
+    double* obs = nullptr;         // per-block partials [blocks][5] or null
 };
-void launch_stage(Domain& d, const StageArgs& a);
+// Returns the number of thread blocks of the launch (= rows of obs partials).
+// *proj_done (if given) tells whether <b|out> was written to a.P_out.
+int launch_stage(Domain& d, const StageArgs& a, bool* proj_done = nullptr);
 int stage_blocks(const Domain& d);
+
+Geo geo_of(const Domain& d);
+
+// TMA-staged stage kernel (k_stage_tma.cu): set up at domain creation; the
+// launch returns false when the grid or row does not tile (then the plain
+// kernel runs).
+void tma_setup(Domain& d);
+void tma_release(Domain& d);
+int tma_blocks(const Domain& d);
+bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done);
+// Tables of the fused nonlocal path (after the projector lists are built).
+void tma_build_nl(Domain& d, const double* D_host);
+bool tma_fused_nl(const Domain& d);
 
 // P[a][i][o] = dV sum_q beta[q][i] w[idx[q]][o]
 void launch_project(Domain& d, const void* w, void* P);

@@ -70,6 +70,31 @@ def test_full_scheme_complex64_all_terms():
     _check_obs(obs, robs, 1e-5)
 
 
+@pytest.mark.parametrize("precision,n,n_orb,order", [
+    ("c64", (16, 8, 12), 32, 4),     # TMA path, 128-byte orbital chunks
+    ("c64", (8, 16, 5), 20, 4),      # TMA path, 64-byte chunks, short z
+    ("c64", (16, 16, 9), 13, 2),     # TMA path, 2nd order, ragged orbital count
+    ("c128", (8, 8, 11), 12, 4),     # TMA path, complex128
+])
+def test_tma_stage_path(precision, n, n_orb, order):
+    """Grids whose x and y extents tile by 8 run the TMA-staged stage kernel;
+    the same case with MLMD_NO_TMA set runs the plain kernel.  Both match the
+    oracle."""
+    import os
+    spec = small_spec(precision=precision, n=n, n_orb=n_orb, fd_order=order, steps=12, n_atoms=5)
+    tol = 1e-12 if precision == "c128" else 1e-5
+    out, obs, ref, robs = _run_both(spec)
+    assert np.max(np.abs(out - ref)) <= tol
+    _check_obs(obs, robs, 1e-11 if precision == "c128" else 1e-5)
+    os.environ["MLMD_NO_TMA"] = "1"
+    try:
+        out2, obs2, _, _ = _run_both(spec)
+    finally:
+        del os.environ["MLMD_NO_TMA"]
+    assert np.max(np.abs(out2 - ref)) <= tol
+    assert np.max(np.abs(out2 - out)) <= tol
+
+
 def test_projector_lists_bit_exact():
     for spec in [small_spec(n_atoms=9, r_cut=1.7), inputs.config("c1", n_orb=8, n_steps=1),
                  inputs.config("c2", n_orb=8, n_steps=1), inputs.config("c4", n_orb=8, n_steps=1)]:
