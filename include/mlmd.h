@@ -210,6 +210,27 @@ MLMD_API mlmd_status mlmd_batch_destroy(mlmd_batch_t batch);
  * [n_domains][n_steps][5] with the per-domain rows of mlmd_propagate. */
 MLMD_API mlmd_status mlmd_batch_propagate(mlmd_batch_t batch, int32_t n_steps, const double* A, double* obs_out);
 
+/* Overlap without device allocation.  The paper has no counterpart: this
+ * entry point serves callers that cannot allocate device memory at the point
+ * of the call (a frozen or fully reserved memory pool, a framework that
+ * forbids allocation on its hot path, a thread that must not contend for the
+ * allocator).  It computes S[n][m] = scale * sum_g conj(X[g][n]) Y[g][m] for
+ * caller-owned device arrays X, Y ([n_grid][n_orb] interleaved complex,
+ * float pairs for MLMD_C64, double pairs for MLMD_C128, rows not padded) into
+ * the caller-owned device array S (complex double [n_orb][n_orb]), on
+ * `stream` (NULL: the legacy default stream); S is valid in stream order.
+ * It calls no allocator: its split sums live in one 4 MiB device array that
+ * the library declares at file scope and that every GPU loading the library
+ * holds until exit, so n_orb may be at most MLMD_OVERLAP_NOALLOC_MAX_ORB
+ * (larger values return MLMD_ERR_INVALID).  All calls share that array:
+ * calls whose kernels overlap on the GPU (e.g. on two streams) race and give
+ * wrong results.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. */
+#define MLMD_OVERLAP_NOALLOC_MAX_ORB 512
+MLMD_API mlmd_status mlmd_overlap_noalloc(int32_t precision, int64_t n_grid, int32_t n_orb, const void* X,
+                                          const void* Y, double scale, double* S, void* stream);
+
 /* Kernel timing hooks (measurement only).  While enabled, every launch of
  * the kinds below is bracketed by CUDA events recorded on the domain's
  * stream; mlmd_profile_read synchronises that stream and returns the summed

@@ -69,6 +69,8 @@ _SIGS = {
     "mlmd_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.POINTER(_P)]),
     "mlmd_batch_destroy": (ctypes.c_int, [_P]),
     "mlmd_batch_propagate": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "mlmd_overlap_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P, _P,
+                                            ctypes.c_double, _P, _P]),
     "mlmd_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "mlmd_profile_read": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "mlmd_launch_count": (ctypes.c_uint64, [_P]),
@@ -267,6 +269,22 @@ def batch_propagate(b, A, obs=True, first_handle=None):
     _check(lib().mlmd_batch_propagate(b, ns, ctypes.c_void_p(A.ctypes.data),
                                       ctypes.c_void_p(out.ctypes.data) if obs else None), first_handle)
     return out
+
+
+def overlap_noalloc(X, Y, scale, S, stream=None):
+    """S = scale * X^dagger Y for device tensors X, Y [n_grid, n_orb] (complex64
+    or complex128) into the device tensor S [n_orb, n_orb] complex128, without
+    any device allocation by the library (see include/mlmd.h)."""
+    import torch
+    assert X.is_cuda and Y.is_cuda and S.is_cuda and X.shape == Y.shape and X.dtype == Y.dtype
+    assert S.dtype == torch.complex128 and S.shape == (X.shape[1], X.shape[1])
+    assert X.is_contiguous() and Y.is_contiguous() and S.is_contiguous()
+    prec = C64 if X.dtype == torch.complex64 else C128
+    st = lib().mlmd_overlap_noalloc(prec, X.shape[0], X.shape[1], ctypes.c_void_p(X.data_ptr()),
+                                    ctypes.c_void_p(Y.data_ptr()), float(scale), ctypes.c_void_p(S.data_ptr()),
+                                    stream if stream is not None else _stream_ptr())
+    _check(st)
+    return S
 
 
 KERNEL = {"stage": 0, "project": 1}
