@@ -290,6 +290,14 @@ void upload_occupations(Domain& d, const std::vector<double>& f) {
     }
 }
 
+// Raise MLMD_ERR_TIMEOUT if a kernel's bounded device-side wait expired
+// (the caller has synchronised the domain's stream).
+void check_err_flag(Domain& d) {
+    int h = 0;
+    MLMD_CUDA(cudaMemcpy(&h, d.err_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    MLMD_REQUIRE(h == 0, MLMD_ERR_TIMEOUT, "a device-side wait timed out");
+}
+
 void check_desc(const mlmd_domain_desc* s) {
     MLMD_REQUIRE(s != nullptr, MLMD_ERR_INVALID, "null descriptor");
     for (int i = 0; i < 3; ++i) MLMD_REQUIRE(s->n[i] >= 4 && s->n[i] <= 4096, MLMD_ERR_INVALID, "grid size out of range");
@@ -554,6 +562,7 @@ mlmd_status mlmd_overlap(mlmd_domain_t d, double* S_out) {
         launch_overlap(*d, d->psi, d->psi, d->desc.h * d->desc.h * d->desc.h, S);
         MLMD_CUDA(cudaMemcpyAsync(S_out, S, sizeof(double) * n * n * 2, cudaMemcpyDeviceToHost, d->stream));
         MLMD_CUDA(cudaStreamSynchronize(d->stream));
+        check_err_flag(*d);
     });
 }
 
@@ -562,6 +571,7 @@ mlmd_status mlmd_reorthonormalize(mlmd_domain_t d, int32_t kind) {
         MLMD_REQUIRE(kind == MLMD_ORTHO_CHOL || kind == MLMD_ORTHO_LOWDIN, MLMD_ERR_INVALID, "bad kind");
         reorth(*d, kind);
         MLMD_CUDA(cudaStreamSynchronize(d->stream));
+        check_err_flag(*d);
     });
 }
 
@@ -575,6 +585,7 @@ mlmd_status mlmd_excitation(mlmd_domain_t d, double* n_exc) {
         std::vector<double> h((size_t)n * n * 2);
         MLMD_CUDA(cudaMemcpyAsync(h.data(), C, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, d->stream));
         MLMD_CUDA(cudaStreamSynchronize(d->stream));
+        check_err_flag(*d);
         double s = 0.0;
         for (size_t i = 0; i < h.size(); ++i) s += h[i] * h[i];
         *n_exc = 2.0 * ((double)n - s);

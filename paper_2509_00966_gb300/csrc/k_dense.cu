@@ -252,6 +252,7 @@ __global__ void k_offdiag_err(const double* __restrict__ T, int n, double* __res
 }  // namespace
 
 void launch_overlap(Domain& d, const void* X, const void* Y, double scale, double* S) {
+    if (launch_overlap_tc(d, X, Y, scale, S)) return;    // tensor cores for the 16-bit GEMM modes
     const int no = d.desc.n_orb;
     const int tiles = (no + 31) / 32;
     // split the grid so that the launch fills the GPU

@@ -222,6 +222,9 @@ void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj
 // S[n][m] = scale * sum_g conj(X[g][n]) Y[g][m] for n, m < n_orb; S is
 // complex double [n_orb][n_orb] on the device.
 void launch_overlap(Domain& d, const void* X, const void* Y, double scale, double* S);
+// The same on the tcgen05 tensor cores with split 16-bit operands, for
+// complex64 domains whose gemm_mode is not FP32 (returns false otherwise).
+bool launch_overlap_tc(Domain& d, const void* X, const void* Y, double scale, double* S);
 // Y[g][m] = sum_n X[g][n] M[n][m] (M complex double [n_orb][n_orb], device)
 void launch_update(Domain& d, const void* X, const double* M, void* Y);
 // In place: S -> lower Cholesky factor L (S = L L^H); returns false if S is

@@ -1,0 +1,63 @@
+"""Tensor-core (tcgen05) Gram/overlap GEMM with split 16-bit operands against
+the FP64 oracle.  Tolerances follow the operand precision: one bf16 part
+(8-bit mantissa) 1e-2, two parts 1e-4, three parts (FP32-class) 2e-5, fp16
+after a power-of-two scale 2e-3, relative to max |S| (= 1 for orthonormal
+orbitals)."""
+import numpy as np
+import pytest
+
+import oracle
+from _helpers import gpu_domain, small_spec, to_device, to_numpy
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16": 1e-2, "bf16x2": 1e-4, "bf16x3": 2e-5, "fp16": 2e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_2509_00966_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def _orth(spec, seed):
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal((spec.n_grid, spec.n_orb)) + 1j * rng.standard_normal((spec.n_grid, spec.n_orb))
+    return oracle.reorth(psi, spec.dV)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x2", "bf16x3", "fp16"])
+@pytest.mark.parametrize("n,n_orb", [((12, 10, 14), 37), ((16, 16, 16), 80), ((24, 20, 16), 150)])
+def test_overlap_tensor_cores(mode, n, n_orb):
+    spec = small_spec(precision="c64", n=n, n_orb=n_orb, steps=1)
+    d, V = gpu_domain(spec, gemm_mode=mode)
+    psi = _orth(spec, 3)
+    # a second, non-orthogonal set in the same span: S is far from identity
+    psi2 = psi @ (np.eye(n_orb) + 0.3 * np.random.default_rng(1).standard_normal((n_orb, n_orb)))
+    for p in (psi, psi2):
+        d.set_orbitals(to_device(p, "c64"))
+        S = d.overlap()
+        Sr = oracle.overlap(p.astype(np.complex64).astype(np.complex128), p.astype(np.complex64).astype(np.complex128),
+                            spec.dV)
+        err = np.max(np.abs(S - Sr)) / np.abs(Sr).max()
+        assert err <= TOL[mode], (mode, err)
+    d.close()
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "fp16"])
+def test_reorth_through_tensor_core_gram(mode):
+    spec = small_spec(precision="c64", n=(16, 16, 12), n_orb=40, steps=1)
+    d, V = gpu_domain(spec, gemm_mode=mode)
+    rng = np.random.default_rng(9)
+    psi = rng.standard_normal((spec.n_grid, 40)) + 1j * rng.standard_normal((spec.n_grid, 40))
+    psi /= np.sqrt(spec.dV * spec.n_grid)
+    d.set_orbitals(to_device(psi, "c64"))
+    d.reorthonormalize("chol")
+    q = to_numpy(d.get_orbitals())
+    qr = oracle.reorth(psi, spec.dV, "chol")
+    tol = 50 * TOL[mode]
+    assert np.max(np.abs(q - qr)) <= tol * np.abs(qr).max()
+    assert np.max(np.abs(spec.dV * q.conj().T @ q - np.eye(40))) <= tol
+    d.close()
