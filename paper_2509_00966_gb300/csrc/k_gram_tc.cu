@@ -12,17 +12,19 @@
 // of a tile accumulate in FP32 in tensor memory; K-slices of the grid go to
 // different CTAs and their FP32 tiles are summed in FP64.
 //
-// Kernel structure: one CTA computes a 128 x 128 tile of G over a K range of
-// grid points.  Per K-step of 64 points, all 256 threads read the FP32 rows
-// of both operands (8 consecutive points of one column per item), split them
-// and store the 16-bit parts in shared memory in the canonical no-swizzle
-// K-major core-matrix layout (8 rows x 16 bytes per core matrix, one 16-byte
-// store per part); thread 0 then issues the tcgen05.mma instructions (M = 128,
-// N = 128, K = 16 each) and commits them to an mbarrier; two buffers let the
-// conversion of the next step overlap the MMAs of this one.  The epilogue
-// reads the accumulator with tcgen05.ld, pairs rows 2a / 2a+1 with a lane
-// shuffle and writes the complex FP64 partial tile.  Every mbarrier wait is
-// bounded; tensor memory is always freed.
+// Structure: a split pass converts each FP32 operand once into its 16-bit
+// parts, stored pre-tiled in device memory: every 128-column x 64-point tile
+// is a 16 KiB image of the canonical no-swizzle K-major core-matrix layout
+// (core matrix = 8 rows x 16 bytes; K-adjacent cores 128 B apart, 8-row
+// groups 1024 B apart).  The GEMM kernel computes one 128 x 128 tile of G
+// over a K range: thread 0 streams the tiles with one bulk copy each into a
+// ring of shared-memory stages (full / empty mbarriers), thread 32 issues
+// the tcgen05.mma instructions (M = N = 128, K = 16, FP32 accumulator in
+// tensor memory) and frees each stage with tcgen05.commit, and the four
+// warps read the accumulator with tcgen05.ld, pair rows 2a / 2a+1 with a lane
+// shuffle and write the complex FP64 partial tile.  For a Gram of one array
+// with itself only the upper-triangular tiles are computed.  Every mbarrier
+// wait is bounded; tensor memory is always freed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -160,26 +162,84 @@ __device__ __forceinline__ uint32_t tile_offset(int row, int k) {
 
 constexpr uint32_t kTileBytes = BM * BK * 2;        // 16 KiB per 16-bit operand tile
 
-// part[z][n][m] (complex FP64) for output tile (tn, tm) of G over K-slice z.
-// Rows of G: real columns [r0, r0 + 128) of X; columns: [c0, c0 + 128) of Y.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Split pass: X (FP32, [N_g][ncols] real) -> parts[p][mt][ks] 16 KiB tile
+// images (128 real columns x 64 grid points, canonical K-major core-matrix
+// layout), zero-padded beyond N_g and ncols.  Block (mt, ks), 256 threads,
+// item = (column c, k-group kg): 8 consecutive points of one column.
 template <int MODE>
-__global__ void __launch_bounds__(256, 1)
-    k_gram_tc(const float* __restrict__ X, const float* __restrict__ Y, int64_t ng, int ld, int n_orb,
-              int64_t kchunk, float fscale, double unscale, double* __restrict__ part, int* __restrict__ err) {
-    constexpr int NPART = Split<MODE>::NPART, NPROD = Split<MODE>::NPROD;
-    constexpr uint32_t STAGE_BYTES = 2 * NPART * kTileBytes;   // A parts + B parts
+__global__ void __launch_bounds__(256) k_split_tiles(const float* __restrict__ X, int64_t ng, int ncols, int nmt,
+                                                     int nks, float fscale, unsigned char* __restrict__ parts) {
+    constexpr int NPART = Split<MODE>::NPART;
+    const int mt = blockIdx.x;
+    const int64_t ks = blockIdx.y;
+    for (int item = threadIdx.x; item < (BK / 8) * BM; item += 256) {
+        const int c = item % BM, kg = item / BM;
+        const int col = mt * BM + c;
+        uint16_t pk[3][8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const int64_t g = ks * BK + kg * 8 + kk;
+            const float x = (g < ng && col < ncols) ? __ldg(X + g * ncols + col) : 0.f;
+            uint16_t pp[3];
+            split_value<MODE>(x, fscale, pp);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) pk[i][kk] = pp[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NPART; ++i) {
+            uint4 w;
+            w.x = pk[i][0] | ((uint32_t)pk[i][1] << 16);
+            w.y = pk[i][2] | ((uint32_t)pk[i][3] << 16);
+            w.z = pk[i][4] | ((uint32_t)pk[i][5] << 16);
+            w.w = pk[i][6] | ((uint32_t)pk[i][7] << 16);
+            unsigned char* tile = parts + (((int64_t)i * nmt + mt) * nks + ks) * kTileBytes;
+            *reinterpret_cast<uint4*>(tile + tile_offset(c, kg * 8)) = w;
+        }
+    }
+}
+
+template <int MODE> struct Stages { static constexpr int value = Split<MODE>::NPART == 1 ? 6 : (Split<MODE>::NPART == 2 ? 3 : 2); };
+
+// part[z][n][m] (complex FP64) for the real output tile (ta, tb) of G = Xr^T Yr
+// over K-slice z.  Thread 0 feeds a ring of STAGES buffers with bulk copies
+// of the pre-split tiles; thread 32 issues the MMAs and frees each buffer
+// with a commit; all four warps read the accumulator at the end.  tri != 0:
+// blockIdx.x enumerates the upper-triangular tile pairs (ta <= tb).
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+    k_gram_tc(const unsigned char* __restrict__ pa, const unsigned char* __restrict__ pb, int nmt, int nks,
+              int ks_per_split, int n_orb, int tri, double unscale, double* __restrict__ part, int* __restrict__ err) {
+    constexpr int NPART = Split<MODE>::NPART, NPROD = Split<MODE>::NPROD, STAGES = Stages<MODE>::value;
+    constexpr uint32_t STAGE_BYTES = 2 * NPART * kTileBytes;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;   // real columns of X (rows of G), of Y
-    const int64_t g0 = (int64_t)blockIdx.z * kchunk;
-    const int64_t g1 = min(ng, g0 + kchunk);
-    const int nsteps = (int)((g1 - g0 + BK - 1) / BK);
-    const int ncols_real = 2 * ld;
+    int ta, tb;
+    if (tri) {          // blockIdx.x -> (ta, tb), ta <= tb, row-major over the upper triangle
+        int r = blockIdx.x, a = 0;
+        while (r >= nmt - a) { r -= nmt - a; ++a; }
+        ta = a;
+        tb = a + r;
+    } else {
+        ta = blockIdx.x / nmt;
+        tb = blockIdx.x % nmt;
+    }
+    const int ks0 = blockIdx.y * ks_per_split;
+    const int nsteps = min(ks_per_split, nks - ks0);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -188,8 +248,11 @@ __global__ void __launch_bounds__(256, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&mma_bar[0], 1);
-        mbar_init(&mma_bar[1], 1);
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(&done, 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -199,99 +262,73 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t tmem = tmem_base;
     constexpr uint32_t IDESC = instr_desc(MODE == MLMD_GEMM_FP16 ? 0u : 1u);
 
-    int uses[2] = {0, 0};     // commits issued per buffer (thread 0)
-    for (int s = 0; s < nsteps; ++s) {
-        const int b = s & 1;
-        unsigned char* As = smem + b * STAGE_BYTES;
-        unsigned char* Bs = As + NPART * kTileBytes;
-        // the MMAs that last read this buffer (step s-2) must be complete
-        if (s >= 2) {
-            bool ok = mbar_wait_bounded(&mma_bar[b], (uint32_t)(((s - 2) >> 1) & 1));
-            if (!ok) abort_sh = 1;
-        }
-        __syncthreads();
-        if (abort_sh) break;
-        // stage: item (operand, k-group, column) = 8 consecutive grid points of
-        // one real column, split into 16-bit parts and stored as one 16-byte
-        // core-matrix row per part
-        const int64_t gk = g0 + (int64_t)s * BK;
-        for (int item = tid; item < 2 * (BK / 8) * BM; item += 256) {
-            const int c = item % BM, kg = (item / BM) % (BK / 8), op = item / (BM * (BK / 8));
-            const float* src = op == 0 ? X : Y;
-            const int col = (op == 0 ? r0 : c0) + c;
-            uint16_t pk[3][8];
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const int64_t g = gk + kg * 8 + kk;
-                const float x = (g < g1 && col < ncols_real) ? __ldg(src + g * ncols_real + col) : 0.f;
-                uint16_t pp[3];
-                split_value<MODE>(x, fscale, pp);
-#pragma unroll
-                for (int i = 0; i < 3; ++i) pk[i][kk] = pp[i];
+    if (tid == 0) {                     // producer
+        for (int i = 0; i < nsteps && !abort_sh; ++i) {
+            const int st = i % STAGES;
+            if (i >= STAGES && !mbar_wait_bounded(&empty[st], (uint32_t)((i / STAGES - 1) & 1))) {
+                abort_sh = 1;
+                break;
             }
-            unsigned char* dst = (op == 0 ? As : Bs) + tile_offset(c, kg * 8);
+            unsigned char* As = smem + st * STAGE_BYTES;
+            unsigned char* Bs = As + NPART * kTileBytes;
+            mbar_expect_tx(&full[st], STAGE_BYTES);
+            const int64_t ks = ks0 + i;
 #pragma unroll
-            for (int i = 0; i < NPART; ++i) {
-                uint4 w;
-                w.x = pk[i][0] | ((uint32_t)pk[i][1] << 16);
-                w.y = pk[i][2] | ((uint32_t)pk[i][3] << 16);
-                w.z = pk[i][4] | ((uint32_t)pk[i][5] << 16);
-                w.w = pk[i][6] | ((uint32_t)pk[i][7] << 16);
-                *reinterpret_cast<uint4*>(dst + i * kTileBytes) = w;
+            for (int p = 0; p < NPART; ++p) {
+                bulk_load(As + p * kTileBytes, pa + (((int64_t)p * nmt + ta) * nks + ks) * kTileBytes, kTileBytes,
+                          &full[st]);
+                bulk_load(Bs + p * kTileBytes, pb + (((int64_t)p * nmt + tb) * nks + ks) * kTileBytes, kTileBytes,
+                          &full[st]);
             }
         }
-        fence_async_smem();       // generic-proxy stores -> visible to the tensor cores
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
+    } else if (tid == 32) {             // MMA issuer
+        for (int i = 0; i < nsteps; ++i) {
+            const int st = i % STAGES;
+            if (!mbar_wait_bounded(&full[st], (uint32_t)((i / STAGES) & 1))) {
+                abort_sh = 1;
+                break;
+            }
             tc_fence_after();
+            const uint32_t As = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t Bs = As + NPART * kTileBytes;
 #pragma unroll
-            for (int p = 0; p < NPROD; ++p) {
-                const uint32_t a_base = smem_u32(As + prod_a(p) * kTileBytes);
-                const uint32_t b_base = smem_u32(Bs + prod_b(p) * kTileBytes);
+            for (int p = 0; p < NPROD; ++p)
 #pragma unroll
                 for (int kk = 0; kk < KSTEPS_PER_MMA; ++kk) {
-                    // K = 16 elements = two K-adjacent core matrices = 256 bytes
-                    const uint64_t ad = smem_desc(a_base + kk * 256, 128, 1024);
-                    const uint64_t bd = smem_desc(b_base + kk * 256, 128, 1024);
-                    mma_f16(tmem, ad, bd, IDESC, (s > 0 || p > 0 || kk > 0) ? 1u : 0u);
+                    const uint64_t ad = smem_desc(As + prod_a(p) * kTileBytes + kk * 256, 128, 1024);
+                    const uint64_t bd = smem_desc(Bs + prod_b(p) * kTileBytes + kk * 256, 128, 1024);
+                    mma_f16(tmem, ad, bd, IDESC, (i > 0 || p > 0 || kk > 0) ? 1u : 0u);
                 }
-            }
-            mma_commit(&mma_bar[b]);
-            uses[b]++;
+            mma_commit(&empty[st]);
         }
+        mma_commit(&done);              // all MMAs issued above have completed when this fires
     }
-    // wait for the last commits of both buffers
-    if (tid == 0) {
-        for (int b = 0; b < 2; ++b)
-            if (uses[b] > 0 && !abort_sh) {
-                if (!mbar_wait_bounded(&mma_bar[b], (uint32_t)((uses[b] - 1) & 1))) abort_sh = 1;
-            }
-    }
+    __syncthreads();
+    if (!abort_sh && nsteps > 0 && !mbar_wait_bounded(&done, 0)) abort_sh = 1;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (abort_sh) {
-        if (tid == 0) atomicExch(err, 1);
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // let bulk copies still in flight land (bounded)
+            for (int st = 0; st < STAGES; ++st) (void)mbar_wait_bounded(&full[st], 0);
+        }
     } else if (nsteps > 0) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of the
-        // tile) and columns 64 (w / 4) .. +63
-        const int quarter = warp & 3, half = warp >> 2;
-        const int row = r0 + quarter * 32 + lane;                     // real row of G
-        for (int cb = half * 64; cb < half * 64 + 64; cb += 32) {
+        // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (rows of the tile)
+        const int row = ta * BM + warp * 32 + lane;                   // real row of G
+        for (int cb = 0; cb < BN; cb += 32) {
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb, v);
-            // pair rows 2a (even lane) and 2a+1 (odd lane)
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
 #pragma unroll
             for (int cc = 0; cc < 32; cc += 2) {
                 const float ee = v[cc], eo = v[cc + 1];                 // G[row][2b], G[row][2b+1]
-                const float oe = __shfl_xor_sync(0xffffffffu, ee, 1);  // from the partner row
+                const float oe = __shfl_xor_sync(0xffffffffu, ee, 1);  // the partner row's
                 const float oo = __shfl_xor_sync(0xffffffffu, eo, 1);
                 if ((lane & 1) == 0) {
-                    const int n = row >> 1, m = (c0 + cb + cc) >> 1;
+                    const int n = row >> 1, m = (tb * BN + cb + cc) >> 1;
                     if (n < n_orb && m < n_orb) {
-                        // even row: G[2n][2m] = ee, G[2n][2m+1] = eo; odd row (partner): oe, oo
-                        double* dst = part + (((int64_t)blockIdx.z * n_orb + n) * n_orb + m) * 2;
+                        double* dst = part + (((int64_t)blockIdx.y * n_orb + n) * n_orb + m) * 2;
                         dst[0] = unscale * ((double)ee + (double)oo);
                         dst[1] = unscale * ((double)eo - (double)oe);
                     }
@@ -307,28 +344,63 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int nsplit, int64_t n, double scale,
+// S[n][m] = scale * sum_z part[z][n][m]; with tri, entries below the computed
+// tile triangle are conj(S[m][n]).
+__global__ void k_gram_reduce(const double* __restrict__ part, int nsplit, int n_orb, int tri, double scale,
                               double* __restrict__ S) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < nsplit; ++k) s += part[(int64_t)k * n + e];
-        S[e] = scale * s;
+    const int64_t nn = (int64_t)n_orb * n_orb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(e / n_orb), m = (int)(e % n_orb);
+        const bool mirror = tri && (n / (BM / 2)) > (m / (BN / 2));
+        const int64_t src = mirror ? (int64_t)m * n_orb + n : e;
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < nsplit; ++k) {
+            re += part[((int64_t)k * nn + src) * 2];
+            im += part[((int64_t)k * nn + src) * 2 + 1];
+        }
+        S[e * 2] = scale * re;
+        S[e * 2 + 1] = scale * (mirror ? -im : im);
     }
 }
 
 template <int MODE>
-void launch_mode(Domain& d, const float* X, const float* Y, int64_t kchunk, int nsplit, float fscale, double unscale,
-                 double* part) {
-    constexpr uint32_t smem = 2 * 2 * Split<MODE>::NPART * kTileBytes + 1024;
+void gram_mode(Domain& d, const float* X, const float* Y, double scale, double* S, float fscale, double unscale) {
+    constexpr int NPART = Split<MODE>::NPART, STAGES = Stages<MODE>::value;
+    const int ncols = 2 * d.ld, no = d.desc.n_orb;
+    const int nmt = (ncols + BM - 1) / BM;
+    const int nks = (int)((d.ng + BK - 1) / BK);
+    const bool same = X == Y;
+    const size_t part_bytes = (size_t)NPART * nmt * nks * kTileBytes;
+    unsigned char* pa = (unsigned char*)d.mem.get(part_bytes);
+    unsigned char* pb = same ? pa : (unsigned char*)d.mem.get(part_bytes);
+    k_split_tiles<MODE><<<dim3(nmt, nks), 256, 0, d.stream>>>(X, d.ng, ncols, nmt, nks, fscale, pa);
+    d.launches++;
+    if (!same) {
+        k_split_tiles<MODE><<<dim3(nmt, nks), 256, 0, d.stream>>>(Y, d.ng, ncols, nmt, nks, fscale, pb);
+        d.launches++;
+    }
+    const int tiles = same ? nmt * (nmt + 1) / 2 : nmt * nmt;
+    // about three CTAs per SM (one resident at a time) over tile pairs and K-slices
+    int nsplit = std::max(1, std::min((3 * 152 + tiles / 2) / tiles, nks));
+    const int ks_per_split = (nks + nsplit - 1) / nsplit;
+    nsplit = (nks + ks_per_split - 1) / ks_per_split;
+    double* part = (double*)d.mem.get((size_t)nsplit * no * no * 2 * sizeof(double));
+    constexpr uint32_t smem = STAGES * 2 * NPART * kTileBytes + 1024;
     static bool attr = false;
     if (!attr) {
         MLMD_CUDA(cudaFuncSetAttribute(k_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    const int tiles = (2 * d.ld + BM - 1) / BM;
-    dim3 grid(tiles, tiles, (unsigned)nsplit);
-    k_gram_tc<MODE><<<grid, 256, smem, d.stream>>>(X, Y, d.ng, d.ld, d.desc.n_orb, kchunk, fscale, unscale, part,
-                                                   d.err_flag);
+    k_gram_tc<MODE><<<dim3(tiles, nsplit), 128, smem, d.stream>>>(pa, pb, nmt, nks, ks_per_split, no, same ? 1 : 0,
+                                                                  unscale, part, d.err_flag);
+    const int64_t nn = (int64_t)no * no;
+    k_gram_reduce<<<(int)std::min<int64_t>((nn + 255) / 256, 2048), 256, 0, d.stream>>>(part, nsplit, no, same ? 1 : 0,
+                                                                                      scale, S);
+    d.launches += 2;
+    MLMD_CUDA(cudaGetLastError());
+    d.mem.put(part);
+    if (!same) d.mem.put(pb);
+    d.mem.put(pa);
 }
 
 }  // namespace
@@ -336,14 +408,6 @@ void launch_mode(Domain& d, const float* X, const float* Y, int64_t kchunk, int 
 bool launch_overlap_tc(Domain& d, const void* X, const void* Y, double scale, double* S) {
     const int mode = d.desc.gemm_mode;
     if (!d.c64() || mode == MLMD_GEMM_FP32) return false;
-    const int no = d.desc.n_orb;
-    const int tiles = (2 * d.ld + BM - 1) / BM;
-    // about four CTAs per SM over all tiles and K-slices
-    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + tiles * tiles / 2) / (tiles * tiles),
-                                                            (d.ng + BK - 1) / BK));
-    const int64_t kchunk = ((d.ng + nsplit - 1) / nsplit + BK - 1) / BK * BK;
-    nsplit = (d.ng + kchunk - 1) / kchunk;
-    double* part = (double*)d.mem.get((size_t)nsplit * no * no * 2 * sizeof(double));
     // FP16: a power-of-two scale so that a normalised orbital's entries are O(1)
     float fscale = 1.f;
     double unscale = 1.0;
@@ -356,16 +420,11 @@ bool launch_overlap_tc(Domain& d, const void* X, const void* Y, double scale, do
     const float* Xf = static_cast<const float*>(X);
     const float* Yf = static_cast<const float*>(Y);
     switch (mode) {
-        case MLMD_GEMM_BF16: launch_mode<MLMD_GEMM_BF16>(d, Xf, Yf, kchunk, (int)nsplit, fscale, unscale, part); break;
-        case MLMD_GEMM_BF16X2: launch_mode<MLMD_GEMM_BF16X2>(d, Xf, Yf, kchunk, (int)nsplit, fscale, unscale, part); break;
-        case MLMD_GEMM_BF16X3: launch_mode<MLMD_GEMM_BF16X3>(d, Xf, Yf, kchunk, (int)nsplit, fscale, unscale, part); break;
-        default: launch_mode<MLMD_GEMM_FP16>(d, Xf, Yf, kchunk, (int)nsplit, fscale, unscale, part); break;
+        case MLMD_GEMM_BF16: gram_mode<MLMD_GEMM_BF16>(d, Xf, Yf, scale, S, fscale, unscale); break;
+        case MLMD_GEMM_BF16X2: gram_mode<MLMD_GEMM_BF16X2>(d, Xf, Yf, scale, S, fscale, unscale); break;
+        case MLMD_GEMM_BF16X3: gram_mode<MLMD_GEMM_BF16X3>(d, Xf, Yf, scale, S, fscale, unscale); break;
+        default: gram_mode<MLMD_GEMM_FP16>(d, Xf, Yf, scale, S, fscale, unscale); break;
     }
-    const int64_t n = (int64_t)no * no * 2;
-    k_gram_reduce<<<(int)std::min<int64_t>((n + 255) / 256, 2048), 256, 0, d.stream>>>(part, (int)nsplit, n, scale, S);
-    d.launches += 2;
-    MLMD_CUDA(cudaGetLastError());
-    d.mem.put(part);
     return true;
 }
 

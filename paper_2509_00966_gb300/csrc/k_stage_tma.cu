@@ -158,7 +158,7 @@ __device__ __forceinline__ const float4* nb_ptr(const float4* s, int x, int y, i
 template <typename R> struct TNl {
     const int32_t* pstart;     // [N_g + 1] per-point entry ranges
     const int32_t* slot;       // [n_list] slot of each entry's atom within the point's column
-    const R* beta;             // [n_list][NP] projector values
+    const R* beta;             // [n_list][NP] projector values times D (scatter-back)
     const int32_t* col_start;  // [ncols + 1]
     const int32_t* col_atom;   // global atom ids of each column, ascending
     const R* D;                // [n_atoms][NP]
@@ -445,10 +445,10 @@ __global__ void __launch_bounds__(256, 2)
             for (int e = e0; e < e1; ++e) {
                 const int s = N.slot[e];
                 R b[NPV];
-                load_beta<R, NPV>(N.beta + (int64_t)e * NPV, b);
+                load_beta<R, NPV>(N.beta + (int64_t)e * NPV, b);   // beta * D
 #pragma unroll
                 for (int pi = 0; pi < NPV; ++pi) {
-                    const R bd = b[pi] * sD[s * NPV + pi];
+                    const R bd = b[pi];
 #pragma unroll
                     for (int k = 0; k < NVT; ++k) {
                         Cv<R> pv;
@@ -719,8 +719,9 @@ void tma_build_nl(Domain& d, const double* D_host) {
             const int64_t e = pstart[g] + cur[g]++;
             ent_slot[e] = qslot[q];
             for (int i = 0; i < np; ++i) {
-                if (rs == 4) reinterpret_cast<float*>(ent_beta.data())[e * np + i] = (float)beta[q * np + i];
-                else reinterpret_cast<double*>(ent_beta.data())[e * np + i] = beta[q * np + i];
+                const double bd = beta[q * np + i] * D_host[(int64_t)a * np + i];
+                if (rs == 4) reinterpret_cast<float*>(ent_beta.data())[e * np + i] = (float)bd;
+                else reinterpret_cast<double*>(ent_beta.data())[e * np + i] = bd;
             }
         }
     std::vector<int32_t> col_start(t.ncols + 1, 0), col_atom;
