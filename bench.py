@@ -47,6 +47,10 @@ def _args():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    p.add_argument("--gram", nargs=3, metavar=("N", "N_ORB", "MODE"),
+                   help="time the overlap (Gram) GEMM of an N^3 x N_ORB complex64 domain in gemm MODE")
+    p.add_argument("--suite", action="store_true",
+                   help="also time the other workloads (c0, c2, c3, c4), one JSON line each")
     return p.parse_args()
 
 
@@ -318,10 +322,151 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _timed(fn, reps=1):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def _device_orbitals(n_grid, n_orb, dV, seed, dtype):
+    """Seeded random orbitals generated on the device (normalised; the
+    library's own Cholesky re-orthonormalisation makes them orthonormal)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    rdt = torch.float32 if dtype == torch.complex64 else torch.float64
+    re = torch.randn(n_grid, n_orb, generator=g, device="cuda", dtype=rdt)
+    im = torch.randn(n_grid, n_orb, generator=g, device="cuda", dtype=rdt)
+    return (torch.complex(re, im) / float(np.sqrt(n_grid * dV))).contiguous()
+
+
+def run_suite(args):
+    """Time each of the other workloads through the C ABI (kernel time from the
+    library's CUDA-event hooks); one JSON line per workload."""
+    import torch
+    from paper_2509_00966_gb300 import build, inputs, mlmd
+    build.build()
+    torch.cuda.set_device(0)
+    peak, src = _peaks()
+    lines = []
+
+    def stage_report(d, units_per_step, bytes_per_unit):
+        st, n = mlmd.profile_read(d.handle, "stage")
+        pr, npj = mlmd.profile_read(d.handle, "project")
+        ach = bytes_per_unit * units_per_step * (n / 4) / (st * 1e-3) / 1e9 if st > 0 else None
+        return {"stage_ms_per_launch": st / max(n, 1), "project_ms_total": pr, "stage_achieved_gbs": ach,
+                "stage_frac_of_measured_hbm": ach / peak if ach else None}
+
+    # c0: complex128, local only, 100 steps
+    spec = inputs.config("c0")
+    d = mlmd.Domain.from_spec(spec)
+    d.set_orbitals(torch.from_numpy(inputs.random_orbitals(spec.n_grid, spec.n_orb, spec.dV, spec.seed)).cuda())
+    d.propagate(spec.A[:10])
+    mlmd.profile_enable(d.handle, True)
+    ms, _ = _timed(lambda: d.propagate(spec.A), reps=3)
+    r = stage_report(d, spec.units_per_step, 16 * 11)
+    lines.append({"workload": "c0 16^3 x 32 complex128, 100 steps", "ms_per_run": ms,
+                  "value": spec.units_per_step * 100 / (ms * 1e-3), "unit": UNIT, **r})
+    d.close()
+
+    # c2: 64^3 x 1024 complex64, 128 x 8 projectors, Cholesky every 10 steps, BF16X3 Gram
+    spec = inputs.config("c2", n_steps=20)
+    for mode in ["bf16x3", "fp32"]:
+        V = inputs.gaussian_wells(spec.n, spec.h, spec.wells, spec.well_depth, spec.well_width)
+        d = mlmd.Domain.from_spec(spec, V=V, gemm_mode=mode)
+        d.set_orbitals(_device_orbitals(spec.n_grid, spec.n_orb, spec.dV, spec.seed, torch.complex64))
+        d.reorthonormalize("chol")
+        d.propagate(spec.A[:2])
+        mlmd.profile_enable(d.handle, True)
+        ms, obs = _timed(lambda: d.propagate(spec.A), reps=1)
+        r = stage_report(d, spec.units_per_step, 88)
+        g_ms, _ = _timed(lambda: d.overlap(), reps=2)
+        lines.append({"workload": f"c2 64^3 x 1024 complex64, 128x8 projectors, 20 steps incl. 2 Cholesky "
+                                  f"re-orthonormalisations, gemm_mode={mode}", "ms_per_run": ms,
+                      "value": spec.units_per_step * 20 / (ms * 1e-3), "unit": UNIT, "overlap_ms": g_ms,
+                      "overlap_tflops_complex_equiv": 8.0 * spec.n_orb ** 2 * spec.n_grid / (g_ms * 1e-3) / 1e12,
+                      **r})
+        d.close()
+
+    # c3: 216 uneven domains in one batch, per-step CUDA graph
+    specs = inputs.batched_specs(n_steps=20)
+    doms = []
+    for i, sp in enumerate(specs):
+        dd = mlmd.Domain.from_spec(sp)
+        dd.set_orbitals(_device_orbitals(sp.n_grid, sp.n_orb, sp.dV, 1000 + i, torch.complex64))
+        doms.append(dd)
+    b = mlmd.batch_create([dd.handle for dd in doms])
+    A = np.stack([sp.A for sp in specs])
+    mlmd.batch_propagate(b, A[:, :2], first_handle=doms[0].handle)
+    ms, _ = _timed(lambda: mlmd.batch_propagate(b, A, first_handle=doms[0].handle), reps=1)
+    units = sum(sp.units_per_step for sp in specs)
+    lines.append({"workload": f"c3 {len(specs)} domains N~U{{24..40}}^3, N_o~U{{32..192}}, 20 steps, batched graph",
+                  "ms_per_run": ms, "value": units * 20 / (ms * 1e-3), "unit": UNIT,
+                  "electrons": float(sum(sp.occ.sum() for sp in specs))})
+    mlmd.batch_destroy(b)
+    for dd in doms:
+        dd.close()
+
+    # c4: 32^3 x 128 complex64, 500-step forward + checkpointed adjoint (K = 50)
+    spec = inputs.config("c4")
+    d = mlmd.Domain.from_spec(spec)
+    d.set_orbitals(torch.from_numpy(inputs.random_orbitals(spec.n_grid, spec.n_orb, spec.dV,
+                                                           spec.seed).astype(np.complex64)).cuda())
+    ms, out = _timed(lambda: d.propagate_adjoint(spec.A, spec.ckpt_every), reps=1)
+    lines.append({"workload": "c4 32^3 x 128 complex64, 32x4 projectors, 500 steps forward + adjoint, K=50",
+                  "ms_per_run": ms, "value": spec.units_per_step * 500 / (ms * 1e-3), "unit": UNIT,
+                  "loss": out[0]})
+    d.close()
+    for l in lines:
+        l["peak_hbm_gbs"] = peak
+        l["peak_source"] = src
+        print(json.dumps(l), flush=True)
+
+
+def run_gram(args):
+    """Time mlmd_overlap (Gram S = dV Psi^H Psi) for an N^3 x N_ORB complex64
+    domain in the given gemm mode; reports tensor FLOP/s of the real product
+    (2 (2 ld)^2 N_g per 16-bit product, upper triangle only)."""
+    import torch
+    from paper_2509_00966_gb300 import build, mlmd
+    build.build()
+    n, no, mode = int(args.gram[0]), int(args.gram[1]), args.gram[2]
+    h = 0.35
+    d = mlmd.Domain((n, n, n), h, no, 4, "c64", gemm_mode=mode)
+    d.set_orbitals(_device_orbitals(n ** 3, no, h ** 3, 2, torch.complex64))
+    d.overlap()
+    ms, _ = _timed(lambda: d.overlap(), reps=3)
+    ld = (no + 7) // 8 * 8
+    nmt = (2 * ld + 127) // 128
+    tri = nmt * (nmt + 1) / 2 / (nmt * nmt)
+    nprod = {"bf16": 1, "bf16x2": 3, "bf16x3": 6, "fp16": 1, "fp32": 1}[mode]
+    flops = 2.0 * (2 * ld) ** 2 * n ** 3 * tri * nprod
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    print(json.dumps({"kernel": "overlap", "grid": n, "n_orb": no, "mode": mode, "ms": ms,
+                      "tensor_tflops": flops / (ms * 1e-3) / 1e12, "peak_bf16_tflops": peak,
+                      "frac": flops / (ms * 1e-3) / 1e12 / peak}), flush=True)
+    d.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.gram:
+        run_gram(args)
+    elif args.suite:
+        run_suite(args)
     else:
         run_ours(args)
 
