@@ -501,6 +501,7 @@ mlmd_status mlmd_propagate(mlmd_domain_t d, int32_t n_steps, const double* A, do
         ensure_A(*d, n_steps);
         MLMD_CUDA(cudaMemcpyAsync(d->A_dev, A, sizeof(double) * 3 * n_steps, cudaMemcpyHostToDevice, d->stream));
         if (obs_out) ensure_obs(*d, n_steps);
+        tma_autotune(*d, d->A_dev);
         for (int k = 0; k < n_steps; ++k) {
             const double* Ak = d->A_dev + 3 * k;
             double* row = obs_out ? d->obs_dev + 5 * k : nullptr;

@@ -92,8 +92,9 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         MLMD_CUDA(cudaMemcpyAsync(A_all, A, sizeof(double) * 3 * (size_t)nd * n_steps, cudaMemcpyHostToDevice, st));
         MLMD_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), st));
         MLMD_CUDA(cudaMemsetAsync(obs_cur, 0, sizeof(double) * 5 * nd, st));
-        // projections of the current orbitals, outside the graph, so that the
-        // captured step is the steady-state one
+        // tile choice and projections of the current orbitals, outside the
+        // graph, so that the captured step is the steady-state one
+        for (auto* d : b->doms) tma_autotune(*d, A_all);
         for (auto* d : b->doms)
             if (d->has_nl() && tma_fused_nl(*d) && !d->pa_psi) {
                 launch_project(*d, d->psi, d->Pa);

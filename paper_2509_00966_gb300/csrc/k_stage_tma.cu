@@ -40,6 +40,8 @@ struct TmaMaps {
 struct TmaState {
     bool ok = false;          // tiles divide the grid and the row splits into chunks
     int vp = 0;               // 16-byte vectors per point per chunk (8 or 4)
+    bool vp8_ok = false;      // the row splits into 128-byte chunks
+    bool tuned = false;       // chunk width chosen by timing
     int zc = 0;               // planes per CTA
     int ncols = 0;            // tiles x z-chunks
     std::vector<TmaMaps> maps;
@@ -654,12 +656,16 @@ void tma_setup(Domain& d) {
     t.maps.clear();
     const int nx = d.desc.n[0], ny = d.desc.n[1], nz = d.desc.n[2];
     const size_t row_bytes = (size_t)d.ld * d.elem;
-    t.vp = (row_bytes % 128 == 0) ? 8 : ((row_bytes % 64 == 0 && d.c64()) ? 4 : 0);
+    t.vp8_ok = row_bytes % 128 == 0;
+    t.vp = t.vp8_ok ? 8 : ((row_bytes % 64 == 0 && d.c64()) ? 4 : 0);
     t.ok = t.vp != 0 && nx % TX == 0 && ny % TY == 0 && std::getenv("MLMD_NO_TMA") == nullptr;
+    t.tuned = !(t.vp8_ok && d.c64());      // complex128 rows: 128-byte chunks only
     if (!t.ok) return;
+    // z range per CTA: enough CTAs to fill the GPU, at most 16 planes (fewer
+    // atoms per column keep the staged projections small)
     const int base = (nx / TX) * (ny / TY) * chunks_of(d);
     const int nzch = std::max(1, std::min((608 + base - 1) / base, std::max(1, nz / 4)));
-    t.zc = (nz + nzch - 1) / nzch;
+    t.zc = std::min((nz + nzch - 1) / nzch, 16);
     t.ncols = (nx / TX) * (ny / TY) * ((nz + t.zc - 1) / t.zc);
 }
 
@@ -762,11 +768,20 @@ void tma_build_nl(Domain& d, const double* D_host) {
                 else reinterpret_cast<double*>(pe_beta.data())[e * np + i] = beta[q * np + i];
             }
         }
-    size_t sm;
-    if (d.c64()) sm = (t.vp == 8) ? (np == 4 ? smem_bytes<float, 8, 4>(t.maxs) : smem_bytes<float, 8, 8>(t.maxs))
-                                  : (np == 4 ? smem_bytes<float, 4, 4>(t.maxs) : smem_bytes<float, 4, 8>(t.maxs));
-    else sm = np == 4 ? smem_bytes<double, 8, 4>(t.maxs) : smem_bytes<double, 8, 8>(t.maxs);
-    if (sm > 200 * 1024) return;   // too many atoms per column for the staging: plain kernel
+    size_t sm8 = 0, sm4 = 0;
+    if (d.c64()) {
+        sm8 = np == 4 ? smem_bytes<float, 8, 4>(t.maxs) : smem_bytes<float, 8, 8>(t.maxs);
+        sm4 = np == 4 ? smem_bytes<float, 4, 4>(t.maxs) : smem_bytes<float, 4, 8>(t.maxs);
+    } else {
+        sm8 = sm4 = np == 4 ? smem_bytes<double, 8, 4>(t.maxs) : smem_bytes<double, 8, 8>(t.maxs);
+    }
+    const size_t kMaxSmem = 200 * 1024;
+    if (sm4 > kMaxSmem) return;   // too many atoms per column for the staging: plain kernel
+    if (t.vp == 8 && sm8 > kMaxSmem) {
+        t.vp = 4;                 // only the narrower chunks fit
+        t.vp8_ok = false;
+        t.maps.clear();
+    }
     t.col_start = (int32_t*)d.mem.get(sizeof(int32_t) * col_start.size());
     t.col_atom = (int32_t*)d.mem.get(sizeof(int32_t) * std::max<size_t>(col_atom.size(), 1));
     t.ent_slot = (int32_t*)d.mem.get(sizeof(int32_t) * ent_slot.size());
@@ -818,5 +833,50 @@ bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done) {
     if (proj_done) *proj_done = proj;
     return true;
 }
+
+// Pick the orbital-chunk width (128- or 64-byte rows per CTA) of the TMA
+// stage kernel by timing a few launches of each on the domain's own data.
+// The timed launches read psi and write only the work buffer wb and the
+// projection buffer Pb, which every step overwrites before reading.
+void tma_autotune(Domain& d, const double* Ak) {
+    if (!d.tma || !d.tma->ok || d.tma->tuned) return;
+    TmaState& t = *d.tma;
+    t.tuned = true;
+    if (!t.vp8_ok || !d.c64()) return;
+    const bool nl = d.has_nl();
+    if (nl && !t.nl_ok) return;
+    StageArgs a;
+    a.w = d.psi;
+    a.psi = d.psi;
+    a.out = d.wb;
+    a.P = nl ? d.Pa : nullptr;
+    a.P_out = nl ? d.Pb : nullptr;
+    a.A = Ak;
+    a.gamma_re = 0.0;
+    a.gamma_im = -d.desc.dt;
+    cudaEvent_t e0, e1;
+    MLMD_CUDA(cudaEventCreate(&e0));
+    MLMD_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_vp = t.vp;
+    for (int vp : {8, 4}) {
+        t.vp = vp;
+        t.maps.clear();
+        launch_stage_tma(d, a, nullptr);      // warm-up (also sets the kernel attribute)
+        MLMD_CUDA(cudaEventRecord(e0, d.stream));
+        for (int r = 0; r < 3; ++r) launch_stage_tma(d, a, nullptr);
+        MLMD_CUDA(cudaEventRecord(e1, d.stream));
+        MLMD_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        MLMD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_vp = vp; }
+    }
+    (void)cudaEventDestroy(e0);
+    (void)cudaEventDestroy(e1);
+    t.vp = best_vp;
+    t.maps.clear();
+}
+
+int tma_chunk_bytes(const Domain& d) { return d.tma && d.tma->ok ? d.tma->vp * 16 : 0; }
 
 }  // namespace mlmd

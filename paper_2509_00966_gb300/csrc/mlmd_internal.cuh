@@ -191,6 +191,11 @@ bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done);
 // Tables of the fused nonlocal path (after the projector lists are built).
 void tma_build_nl(Domain& d, const double* D_host);
 bool tma_fused_nl(const Domain& d);
+// Time both orbital-chunk widths of the TMA stage kernel once per domain and
+// keep the faster (no-op after the first call).  Must not run during stream
+// capture.  Ak: device [3].
+void tma_autotune(Domain& d, const double* Ak);
+int tma_chunk_bytes(const Domain& d);
 
 // P[a][i][o] = dV sum_q beta[q][i] w[idx[q]][o]
 void launch_project(Domain& d, const void* w, void* P);
