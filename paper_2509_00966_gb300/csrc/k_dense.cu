@@ -140,54 +140,6 @@ __global__ void __launch_bounds__(256) k_update(const R* __restrict__ X, const d
         }
 }
 
-// ---- FP64 complex Cholesky, column by column (right-looking) ----------------
-// S is row-major complex [n][n]; on exit its lower triangle holds L.
-__global__ void k_chol_col(double* __restrict__ S, int n, int j, int* __restrict__ info) {
-    __shared__ double dj;
-    if (threadIdx.x == 0) {
-        const double a = S[((int64_t)j * n + j) * 2];
-        if (!(a > 0.0) || !isfinite(a)) { if (*info == 0) *info = j + 1; dj = 1.0; }
-        else dj = sqrt(a);
-        S[((int64_t)j * n + j) * 2] = dj;
-        S[((int64_t)j * n + j) * 2 + 1] = 0.0;
-    }
-    __syncthreads();
-    const double inv = 1.0 / dj;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-        S[((int64_t)i * n + j) * 2] *= inv;
-        S[((int64_t)i * n + j) * 2 + 1] *= inv;
-    }
-}
-
-// S[i][k] -= L[i][j] conj(L[k][j]) for j < k <= i
-__global__ void k_chol_update(double* __restrict__ S, int n, int j) {
-    const int i = j + 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = j + 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || k > i) return;
-    const double ar = S[((int64_t)i * n + j) * 2], ai = S[((int64_t)i * n + j) * 2 + 1];
-    const double br = S[((int64_t)k * n + j) * 2], bi = -S[((int64_t)k * n + j) * 2 + 1];
-    S[((int64_t)i * n + k) * 2] -= ar * br - ai * bi;
-    S[((int64_t)i * n + k) * 2 + 1] -= ar * bi + ai * br;
-}
-
-// Row i of X = L^{-1} by forward substitution: X[i][c] = (delta_ic - sum_{c<=k<i} L[i][k] X[k][c]) / L[i][i]
-__global__ void k_trinv_row(const double* __restrict__ L, double* __restrict__ X, int n, int i) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        double sr = (c == i) ? 1.0 : 0.0, si = 0.0;
-        if (c < i) {
-            for (int k = c; k < i; ++k) {
-                const double lr = L[((int64_t)i * n + k) * 2], li = L[((int64_t)i * n + k) * 2 + 1];
-                const double xr = X[((int64_t)k * n + c) * 2], xi = X[((int64_t)k * n + c) * 2 + 1];
-                sr -= lr * xr - li * xi;
-                si -= lr * xi + li * xr;
-            }
-        }
-        const double d = L[((int64_t)i * n + i) * 2];
-        X[((int64_t)i * n + c) * 2] = c <= i ? sr / d : 0.0;
-        X[((int64_t)i * n + c) * 2 + 1] = c <= i ? si / d : 0.0;
-    }
-}
-
 // Minv[r][c] = conj(X[c][r])
 __global__ void k_conj_transpose(const double* __restrict__ X, int n, double* __restrict__ Y) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -249,6 +201,219 @@ __global__ void k_offdiag_err(const double* __restrict__ T, int n, double* __res
     }
 }
 
+// ---- blocked FP64 complex Cholesky (panel width 32) ---------------------------
+constexpr int CB = 32;
+
+// Block column kb: every CTA loads the (already updated) 32 x 32 diagonal
+// block, factors it in shared memory, and solves its own 32 rows of the
+// panel below, L21 = A21 L11^{-H}.  A second single-CTA launch
+// (write_l11 = 1) stores L11 once no CTA of the first still reads A11.
+// info > 0 marks a non-positive pivot.
+__global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int n, int kb, int* __restrict__ info,
+                                                    int write_l11) {
+    __shared__ double L[CB][CB][2];
+    __shared__ double rows[CB][CB][2];
+    const int c0 = kb * CB;
+    const int nb = min(CB, n - c0);
+    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+        const int i = e / CB, j = e % CB;
+        const bool in = i < nb && j < nb;
+        L[i][j][0] = in ? S[((int64_t)(c0 + i) * n + c0 + j) * 2] : 0.0;
+        L[i][j][1] = in ? S[((int64_t)(c0 + i) * n + c0 + j) * 2 + 1] : 0.0;
+    }
+    __syncthreads();
+    // unblocked right-looking factorisation of the diagonal block
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            double a = L[j][j][0];
+            if (!(a > 0.0) || !isfinite(a)) { if (atomicCAS(info, 0, c0 + j + 1) == 0) {} a = 1.0; }
+            L[j][j][0] = sqrt(a);
+            L[j][j][1] = 0.0;
+        }
+        __syncthreads();
+        const double inv = 1.0 / L[j][j][0];
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) { L[i][j][0] *= inv; L[i][j][1] *= inv; }
+        __syncthreads();
+        for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+            const int i = e / CB, k = e % CB;
+            if (i > j && k > j && k <= i && i < nb) {
+                const double ar = L[i][j][0], ai = L[i][j][1], br = L[k][j][0], bi = -L[k][j][1];
+                L[i][k][0] -= ar * br - ai * bi;
+                L[i][k][1] -= ar * bi + ai * br;
+            }
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && write_l11) {
+        // the last CTA stores L11 only after every CTA has read the block:
+        // launched separately (write_l11 = 1) with a single CTA
+        for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+            const int i = e / nb, j = e % nb;
+            if (j <= i) {
+                S[((int64_t)(c0 + i) * n + c0 + j) * 2] = L[i][j][0];
+                S[((int64_t)(c0 + i) * n + c0 + j) * 2 + 1] = L[i][j][1];
+            }
+        }
+        return;
+    }
+    // panel rows r0 .. r0+31 below the diagonal block
+    const int r0 = c0 + nb + blockIdx.x * CB;
+    if (r0 >= n) return;
+    const int nr = min(CB, n - r0);
+    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+        const int i = e / CB, j = e % CB;
+        const bool in = i < nr && j < nb;
+        rows[i][j][0] = in ? S[((int64_t)(r0 + i) * n + c0 + j) * 2] : 0.0;
+        rows[i][j][1] = in ? S[((int64_t)(r0 + i) * n + c0 + j) * 2 + 1] : 0.0;
+    }
+    __syncthreads();
+    // x L11^H = a  ->  x_j = (a_j - sum_{k<j} x_k conj(L11[j][k])) / L11[j][j]
+    if (threadIdx.x < nr) {
+        const int i = threadIdx.x;
+        for (int j = 0; j < nb; ++j) {
+            double sr = rows[i][j][0], si = rows[i][j][1];
+            for (int k = 0; k < j; ++k) {
+                const double xr = rows[i][k][0], xi = rows[i][k][1];
+                const double lr = L[j][k][0], li = -L[j][k][1];
+                sr -= xr * lr - xi * li;
+                si -= xr * li + xi * lr;
+            }
+            const double d = L[j][j][0];
+            rows[i][j][0] = sr / d;
+            rows[i][j][1] = si / d;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        S[((int64_t)(r0 + i) * n + c0 + j) * 2] = rows[i][j][0];
+        S[((int64_t)(r0 + i) * n + c0 + j) * 2 + 1] = rows[i][j][1];
+    }
+}
+
+// Trailing update after block column kb: S[i][k] -= sum_j L[i][j] conj(L[k][j])
+// for i >= k >= (kb+1)*32 (lower triangle), j over the panel.  32 x 32 output
+// tiles, 256 threads, 4 outputs each.
+__global__ void __launch_bounds__(256) k_chol_trail(double* __restrict__ S, int n, int kb) {
+    const int c0 = kb * CB, nb = min(CB, n - c0);
+    const int base = c0 + nb;
+    const int ti = blockIdx.y, tk = blockIdx.x;
+    if (tk > ti) return;
+    const int i0 = base + ti * CB, k0 = base + tk * CB;
+    if (i0 >= n || k0 >= n) return;
+    __shared__ double Li[CB][CB + 1][2], Lk[CB][CB + 1][2];
+    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+        const int r = e / CB, j = e % CB;
+        const bool ini = i0 + r < n && j < nb, ink = k0 + r < n && j < nb;
+        Li[r][j][0] = ini ? S[((int64_t)(i0 + r) * n + c0 + j) * 2] : 0.0;
+        Li[r][j][1] = ini ? S[((int64_t)(i0 + r) * n + c0 + j) * 2 + 1] : 0.0;
+        Lk[r][j][0] = ink ? S[((int64_t)(k0 + r) * n + c0 + j) * 2] : 0.0;
+        Lk[r][j][1] = ink ? S[((int64_t)(k0 + r) * n + c0 + j) * 2 + 1] : 0.0;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < CB * CB; o += blockDim.x) {
+        const int r = o / CB, c = o % CB;
+        const int i = i0 + r, k = k0 + c;
+        if (i >= n || k >= n || k > i) continue;
+        double sr = 0.0, si = 0.0;
+        for (int j = 0; j < nb; ++j) {
+            const double ar = Li[r][j][0], ai = Li[r][j][1], br = Lk[c][j][0], bi = -Lk[c][j][1];
+            sr += ar * br - ai * bi;
+            si += ar * bi + ai * br;
+        }
+        S[((int64_t)i * n + k) * 2] -= sr;
+        S[((int64_t)i * n + k) * 2 + 1] -= si;
+    }
+}
+
+// X = L^{-1} (lower) by 32 x 32 blocks.  Diagonal blocks first (one CTA per
+// block, thread c solves column c by forward substitution), then, for block
+// offset d = 1, 2, ..., every block (i, j = i - d) in parallel:
+// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj.
+__global__ void __launch_bounds__(32) k_trinv_diag(const double* __restrict__ L, double* __restrict__ X, int n) {
+    __shared__ double Lb[CB][CB][2];
+    const int b0 = blockIdx.x * CB, nb = min(CB, n - b0);
+    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+        const int i = e / CB, j = e % CB;
+        const bool in = i < nb && j < nb;
+        Lb[i][j][0] = in ? L[((int64_t)(b0 + i) * n + b0 + j) * 2] : (i == j ? 1.0 : 0.0);
+        Lb[i][j][1] = in ? L[((int64_t)(b0 + i) * n + b0 + j) * 2 + 1] : 0.0;
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    double xr[CB], xi[CB];
+    for (int i = 0; i < CB; ++i) {
+        double sr = (i == c) ? 1.0 : 0.0, si = 0.0;
+        for (int k = c; k < i; ++k) {
+            sr -= Lb[i][k][0] * xr[k] - Lb[i][k][1] * xi[k];
+            si -= Lb[i][k][0] * xi[k] + Lb[i][k][1] * xr[k];
+        }
+        xr[i] = i >= c ? sr / Lb[i][i][0] : 0.0;
+        xi[i] = i >= c ? si / Lb[i][i][0] : 0.0;
+    }
+    if (c < nb)
+        for (int i = 0; i < nb; ++i) {
+            X[((int64_t)(b0 + i) * n + b0 + c) * 2] = xr[i];
+            X[((int64_t)(b0 + i) * n + b0 + c) * 2 + 1] = xi[i];
+        }
+}
+
+__global__ void __launch_bounds__(256) k_trinv_off(const double* __restrict__ L, double* __restrict__ X, int n, int d) {
+    __shared__ double A[CB][CB + 1][2], B[CB][CB + 1][2];
+    const int jb = blockIdx.x, ib = jb + d;
+    const int i0 = ib * CB, j0 = jb * CB;
+    const int ni = min(CB, n - i0), nj = min(CB, n - j0);
+    double tr[4] = {0, 0, 0, 0}, ti[4] = {0, 0, 0, 0};
+    for (int kb = jb; kb < ib; ++kb) {
+        const int k0 = kb * CB, nk = min(CB, n - k0);
+        for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+            const int r = e / CB, c = e % CB;
+            const bool ina = r < ni && c < nk, inb = r < nk && c < nj;
+            A[r][c][0] = ina ? L[((int64_t)(i0 + r) * n + k0 + c) * 2] : 0.0;
+            A[r][c][1] = ina ? L[((int64_t)(i0 + r) * n + k0 + c) * 2 + 1] : 0.0;
+            B[r][c][0] = inb ? X[((int64_t)(k0 + r) * n + j0 + c) * 2] : 0.0;
+            B[r][c][1] = inb ? X[((int64_t)(k0 + r) * n + j0 + c) * 2 + 1] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int o = threadIdx.x + 256 * q, r = o / CB, c = o % CB;
+            for (int k = 0; k < CB; ++k) {
+                tr[q] += A[r][k][0] * B[k][c][0] - A[r][k][1] * B[k][c][1];
+                ti[q] += A[r][k][0] * B[k][c][1] + A[r][k][1] * B[k][c][0];
+            }
+        }
+        __syncthreads();
+    }
+    // T into B, X_ii into A, then X_ij = -X_ii T
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = threadIdx.x + 256 * q, r = o / CB, c = o % CB;
+        B[r][c][0] = tr[q];
+        B[r][c][1] = ti[q];
+    }
+    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+        const int r = e / CB, c = e % CB;
+        const bool in = r < ni && c < ni;
+        A[r][c][0] = in ? X[((int64_t)(i0 + r) * n + i0 + c) * 2] : 0.0;
+        A[r][c][1] = in ? X[((int64_t)(i0 + r) * n + i0 + c) * 2 + 1] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = threadIdx.x + 256 * q, r = o / CB, c = o % CB;
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k < CB; ++k) {
+            sr += A[r][k][0] * B[k][c][0] - A[r][k][1] * B[k][c][1];
+            si += A[r][k][0] * B[k][c][1] + A[r][k][1] * B[k][c][0];
+        }
+        if (r < ni && c < nj) {
+            X[((int64_t)(i0 + r) * n + j0 + c) * 2] = -sr;
+            X[((int64_t)(i0 + r) * n + j0 + c) * 2 + 1] = -si;
+        }
+    }
+}
+
 }  // namespace
 
 void launch_overlap(Domain& d, const void* X, const void* Y, double scale, double* S) {
@@ -285,20 +450,28 @@ void launch_update(Domain& d, const void* X, const double* M, void* Y) {
 void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info) {
     const int n = d.desc.n_orb;
     MLMD_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), d.stream));
-    for (int j = 0; j < n; ++j) {
-        k_chol_col<<<1, 256, 0, d.stream>>>(S, n, j, d_info);
+    const int nblk = (n + CB - 1) / CB;
+    for (int kb = 0; kb < nblk; ++kb) {
+        const int below = n - (kb * CB + std::min(CB, n - kb * CB));
+        if (below > 0) {
+            k_chol_panel<<<(below + CB - 1) / CB, 256, 0, d.stream>>>(S, n, kb, d_info, 0);
+            d.launches++;
+        }
+        k_chol_panel<<<1, 256, 0, d.stream>>>(S, n, kb, d_info, 1);
         d.launches++;
-        const int m = n - j - 1;
-        if (m > 0) {
-            dim3 blk(16, 16), grd((m + 15) / 16, (m + 15) / 16);
-            k_chol_update<<<grd, blk, 0, d.stream>>>(S, n, j);
+        if (below > 0) {
+            const int t = (below + CB - 1) / CB;
+            k_chol_trail<<<dim3(t, t), 256, 0, d.stream>>>(S, n, kb);
             d.launches++;
         }
     }
-    // X = L^{-1} row by row into Minv's storage, then Minv = X^H
+    // X = L^{-1} (blocked wavefront), then Minv = X^H
     double* X = (double*)d.mem.get((size_t)n * n * 2 * sizeof(double));
-    for (int i = 0; i < n; ++i) {
-        k_trinv_row<<<(n + 255) / 256, 256, 0, d.stream>>>(S, X, n, i);
+    MLMD_CUDA(cudaMemsetAsync(X, 0, (size_t)n * n * 2 * sizeof(double), d.stream));
+    k_trinv_diag<<<nblk, 32, 0, d.stream>>>(S, X, n);
+    d.launches++;
+    for (int dd = 1; dd < nblk; ++dd) {
+        k_trinv_off<<<nblk - dd, 256, 0, d.stream>>>(S, X, n, dd);
         d.launches++;
     }
     k_conj_transpose<<<(int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096), 256, 0, d.stream>>>(X, n, Minv);
