@@ -205,61 +205,27 @@ __global__ void k_offdiag_err(const double* __restrict__ T, int n, double* __res
 constexpr int CB = 32;
 
 // Block column kb: every CTA loads the (already updated) 32 x 32 diagonal
-// block, factors it in shared memory, and solves its own 32 rows of the
-// panel below, L21 = A21 L11^{-H}.  A second single-CTA launch
-// (write_l11 = 1) stores L11 once no CTA of the first still reads A11.
+// block A11 and factors it in shared memory (all threads; FP64 issues slowly,
+// so no step runs on a single warp), then solves its own 32 panel rows
+// L21 L11^H = A21 column by column (right-looking: every thread updates its
+// share of the rows after each column).  CTA 0 stores L11 in Ld[kb], a side
+// array, so that no CTA overwrites A11 while another still reads it.
 // info > 0 marks a non-positive pivot.
-__global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int n, int kb, int* __restrict__ info,
-                                                    int write_l11) {
-    __shared__ double L[CB][CB][2];
-    __shared__ double rows[CB][CB][2];
+__global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int n, int kb, double* __restrict__ Ld,
+                                                    int* __restrict__ info) {
+    __shared__ double L[CB][CB + 1][2];
+    __shared__ double rows[CB][CB + 1][2];
     const int c0 = kb * CB;
     const int nb = min(CB, n - c0);
     for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
         const int i = e / CB, j = e % CB;
         const bool in = i < nb && j < nb;
-        L[i][j][0] = in ? S[((int64_t)(c0 + i) * n + c0 + j) * 2] : 0.0;
+        L[i][j][0] = in ? S[((int64_t)(c0 + i) * n + c0 + j) * 2] : (i == j ? 1.0 : 0.0);
         L[i][j][1] = in ? S[((int64_t)(c0 + i) * n + c0 + j) * 2 + 1] : 0.0;
     }
-    __syncthreads();
-    // unblocked right-looking factorisation of the diagonal block
-    for (int j = 0; j < nb; ++j) {
-        if (threadIdx.x == 0) {
-            double a = L[j][j][0];
-            if (!(a > 0.0) || !isfinite(a)) { if (atomicCAS(info, 0, c0 + j + 1) == 0) {} a = 1.0; }
-            L[j][j][0] = sqrt(a);
-            L[j][j][1] = 0.0;
-        }
-        __syncthreads();
-        const double inv = 1.0 / L[j][j][0];
-        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) { L[i][j][0] *= inv; L[i][j][1] *= inv; }
-        __syncthreads();
-        for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-            const int i = e / CB, k = e % CB;
-            if (i > j && k > j && k <= i && i < nb) {
-                const double ar = L[i][j][0], ai = L[i][j][1], br = L[k][j][0], bi = -L[k][j][1];
-                L[i][k][0] -= ar * br - ai * bi;
-                L[i][k][1] -= ar * bi + ai * br;
-            }
-        }
-        __syncthreads();
-    }
-    if (blockIdx.x == gridDim.x - 1 && write_l11) {
-        // the last CTA stores L11 only after every CTA has read the block:
-        // launched separately (write_l11 = 1) with a single CTA
-        for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-            const int i = e / nb, j = e % nb;
-            if (j <= i) {
-                S[((int64_t)(c0 + i) * n + c0 + j) * 2] = L[i][j][0];
-                S[((int64_t)(c0 + i) * n + c0 + j) * 2 + 1] = L[i][j][1];
-            }
-        }
-        return;
-    }
-    // panel rows r0 .. r0+31 below the diagonal block
+    // this CTA's panel rows r0 .. r0+31 below the diagonal block
     const int r0 = c0 + nb + blockIdx.x * CB;
-    if (r0 >= n) return;
-    const int nr = min(CB, n - r0);
+    const int nr = r0 < n ? min(CB, n - r0) : 0;
     for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
         const int i = e / CB, j = e % CB;
         const bool in = i < nr && j < nb;
@@ -267,23 +233,51 @@ __global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int 
         rows[i][j][1] = in ? S[((int64_t)(r0 + i) * n + c0 + j) * 2 + 1] : 0.0;
     }
     __syncthreads();
-    // x L11^H = a  ->  x_j = (a_j - sum_{k<j} x_k conj(L11[j][k])) / L11[j][j]
-    if (threadIdx.x < nr) {
-        const int i = threadIdx.x;
-        for (int j = 0; j < nb; ++j) {
-            double sr = rows[i][j][0], si = rows[i][j][1];
-            for (int k = 0; k < j; ++k) {
-                const double xr = rows[i][k][0], xi = rows[i][k][1];
-                const double lr = L[j][k][0], li = -L[j][k][1];
-                sr -= xr * lr - xi * li;
-                si -= xr * li + xi * lr;
-            }
-            const double d = L[j][j][0];
-            rows[i][j][0] = sr / d;
-            rows[i][j][1] = si / d;
+    // right-looking factorisation of the diagonal block
+    for (int j = 0; j < nb; ++j) {
+        if (threadIdx.x == 0) {
+            double a = L[j][j][0];
+            if (!(a > 0.0) || !isfinite(a)) { atomicCAS(info, 0, c0 + j + 1); a = 1.0; }
+            L[j][j][0] = sqrt(a);
+            L[j][j][1] = 0.0;
         }
+        __syncthreads();
+        const double inv = 1.0 / L[j][j][0];
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) { L[i][j][0] *= inv; L[i][j][1] *= inv; }
+        __syncthreads();
+        const int m = nb - j - 1;                         // trailing rows/cols of the block
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) {
+                const double ar = L[i][j][0], ai = L[i][j][1], br = L[k][j][0], bi = -L[k][j][1];
+                L[i][k][0] -= ar * br - ai * bi;
+                L[i][k][1] -= ar * bi + ai * br;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+            const int i = e / CB, j = e % CB;
+            Ld[((int64_t)kb * CB * CB + e) * 2] = (j <= i) ? L[i][j][0] : 0.0;
+            Ld[((int64_t)kb * CB * CB + e) * 2 + 1] = (j <= i) ? L[i][j][1] : 0.0;
+        }
+    if (nr == 0) return;
+    // x L11^H = a, column by column: x_j = a_j / L_jj, then a_k -= x_j conj(L_kj), k > j
+    for (int j = 0; j < nb; ++j) {
+        const double dinv = 1.0 / L[j][j][0];
+        if (threadIdx.x < CB) { rows[threadIdx.x][j][0] *= dinv; rows[threadIdx.x][j][1] *= dinv; }
+        __syncthreads();
+        const int m = nb - j - 1;
+        for (int e = threadIdx.x; e < CB * m; e += blockDim.x) {
+            const int i = e / m, k = j + 1 + e % m;
+            const double xr = rows[i][j][0], xi = rows[i][j][1];
+            const double lr = L[k][j][0], li = -L[k][j][1];
+            rows[i][k][0] -= xr * lr - xi * li;
+            rows[i][k][1] -= xr * li + xi * lr;
+        }
+        __syncthreads();
+    }
     for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
         const int i = e / nb, j = e % nb;
         S[((int64_t)(r0 + i) * n + c0 + j) * 2] = rows[i][j][0];
@@ -326,92 +320,139 @@ __global__ void __launch_bounds__(256) k_chol_trail(double* __restrict__ S, int 
     }
 }
 
-// X = L^{-1} (lower) by 32 x 32 blocks.  Diagonal blocks first (one CTA per
-// block, thread c solves column c by forward substitution), then, for block
-// offset d = 1, 2, ..., every block (i, j = i - d) in parallel:
-// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj.
-__global__ void __launch_bounds__(32) k_trinv_diag(const double* __restrict__ L, double* __restrict__ X, int n) {
-    __shared__ double Lb[CB][CB][2];
-    const int b0 = blockIdx.x * CB, nb = min(CB, n - b0);
+// X = L^{-1} (lower), recursively by blocks.  First every 32 x 32 diagonal
+// block X_ii = L_ii^{-1} (k_trinv_diag, from the stored L11 blocks); then for
+// block size b = 32, 64, ...: pair p joins the finished inverses of
+// A = [2pb, 2pb + b) and C = [2pb + b, 2pb + 2b) into one of size 2b through
+//     X_CA = -X_CC (L_CA X_AA)
+// (k_trinv_t: T = L_CA X_AA, then k_trinv_x: X_CA = -X_CC T), two batched
+// GEMMs over all pairs of the level, each skipping the zero triangles.
+__global__ void __launch_bounds__(256) k_trinv_diag(const double* __restrict__ Ld, double* __restrict__ X, int n) {
+    __shared__ double Lb[CB][CB + 1][2];
+    __shared__ double Xb[CB][CB + 1][2];
+    const int kb = blockIdx.x, b0 = kb * CB, nb = min(CB, n - b0);
     for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
         const int i = e / CB, j = e % CB;
-        const bool in = i < nb && j < nb;
-        Lb[i][j][0] = in ? L[((int64_t)(b0 + i) * n + b0 + j) * 2] : (i == j ? 1.0 : 0.0);
-        Lb[i][j][1] = in ? L[((int64_t)(b0 + i) * n + b0 + j) * 2 + 1] : 0.0;
+        Lb[i][j][0] = Ld[((int64_t)kb * CB * CB + e) * 2];
+        Lb[i][j][1] = Ld[((int64_t)kb * CB * CB + e) * 2 + 1];
+        Xb[i][j][0] = (i == j) ? 1.0 : 0.0;     // right-hand sides: the identity
+        Xb[i][j][1] = 0.0;
     }
     __syncthreads();
-    const int c = threadIdx.x;
-    double xr[CB], xi[CB];
+    // forward substitution on all 32 columns at once: row i of X is final
+    // after step i, then rows below take their update
     for (int i = 0; i < CB; ++i) {
-        double sr = (i == c) ? 1.0 : 0.0, si = 0.0;
-        for (int k = c; k < i; ++k) {
-            sr -= Lb[i][k][0] * xr[k] - Lb[i][k][1] * xi[k];
-            si -= Lb[i][k][0] * xi[k] + Lb[i][k][1] * xr[k];
+        const double dinv = 1.0 / Lb[i][i][0];
+        if (threadIdx.x < CB) { Xb[i][threadIdx.x][0] *= dinv; Xb[i][threadIdx.x][1] *= dinv; }
+        __syncthreads();
+        const int m = CB - i - 1;
+        for (int e = threadIdx.x; e < m * CB; e += blockDim.x) {
+            const int r = i + 1 + e / CB, c = e % CB;
+            const double lr = Lb[r][i][0], li = Lb[r][i][1], xr = Xb[i][c][0], xi = Xb[i][c][1];
+            Xb[r][c][0] -= lr * xr - li * xi;
+            Xb[r][c][1] -= lr * xi + li * xr;
         }
-        xr[i] = i >= c ? sr / Lb[i][i][0] : 0.0;
-        xi[i] = i >= c ? si / Lb[i][i][0] : 0.0;
+        __syncthreads();
     }
-    if (c < nb)
-        for (int i = 0; i < nb; ++i) {
-            X[((int64_t)(b0 + i) * n + b0 + c) * 2] = xr[i];
-            X[((int64_t)(b0 + i) * n + b0 + c) * 2 + 1] = xi[i];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, c = e % nb;
+        X[((int64_t)(b0 + i) * n + b0 + c) * 2] = Xb[i][c][0];
+        X[((int64_t)(b0 + i) * n + b0 + c) * 2 + 1] = Xb[i][c][1];
+    }
+}
+
+// acc += A[r0.., k0..k0+31] B[k0..k0+31, c0..] for one 32 x 32 output tile,
+// each of the 256 threads holding a 2 x 2 block of outputs (rows ty, ty+16;
+// columns tx, tx+16).  Out-of-range entries load as zero.
+struct Tile32 {
+    double a[CB][CB + 1][2];
+    double b[CB][CB + 1][2];
+};
+
+__device__ __forceinline__ void tile_mac(Tile32& t, const double* A, int lda, int ar, int ac, int arows, int acols,
+                                         const double* B, int ldb, int br, int bc, int brows, int bcols,
+                                         double (&acc)[2][2][2]) {
+    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+        const int r = e / CB, c = e % CB;
+        const bool ina = r < arows && c < acols, inb = r < brows && c < bcols;
+        t.a[r][c][0] = ina ? A[((int64_t)(ar + r) * lda + ac + c) * 2] : 0.0;
+        t.a[r][c][1] = ina ? A[((int64_t)(ar + r) * lda + ac + c) * 2 + 1] : 0.0;
+        t.b[r][c][0] = inb ? B[((int64_t)(br + r) * ldb + bc + c) * 2] : 0.0;
+        t.b[r][c][1] = inb ? B[((int64_t)(br + r) * ldb + bc + c) * 2 + 1] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 4
+    for (int k = 0; k < CB; ++k) {
+        double xr[2], xi[2], yr[2], yi[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            xr[q] = t.a[ty + 16 * q][k][0]; xi[q] = t.a[ty + 16 * q][k][1];
+            yr[q] = t.b[k][tx + 16 * q][0]; yi[q] = t.b[k][tx + 16 * q][1];
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                acc[p][q][0] += xr[p] * yr[q] - xi[p] * yi[q];
+                acc[p][q][1] += xr[p] * yi[q] + xi[p] * yr[q];
+            }
+    }
+    __syncthreads();
+}
+
+// T_p = L_CA X_AA for every pair p of level b (T_p: [nc][b], leading dim b).
+// X_AA is lower triangular: only k >= the output column tile contributes.
+// Grid (b/32, b/32, pairs).
+__global__ void __launch_bounds__(256) k_trinv_t(const double* __restrict__ L, const double* __restrict__ X, int n,
+                                                 int b, double* __restrict__ T) {
+    __shared__ Tile32 t;
+    const int p = blockIdx.z, a0 = 2 * p * b, cc0 = a0 + b;
+    const int nc = min(b, n - cc0);
+    const int ti = blockIdx.y * CB, tj = blockIdx.x * CB;
+    if (ti >= nc) return;
+    double acc[2][2][2] = {};
+    for (int k0 = tj; k0 < b; k0 += CB)
+        tile_mac(t, L, n, cc0 + ti, a0 + k0, min(CB, nc - ti), CB, X, n, a0 + k0, a0 + tj, CB, CB, acc);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double* Tp = T + (int64_t)p * b * b * 2;
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = ti + ty + 16 * pp, c = tj + tx + 16 * q;
+            if (r < nc) {
+                Tp[((int64_t)r * b + c) * 2] = acc[pp][q][0];
+                Tp[((int64_t)r * b + c) * 2 + 1] = acc[pp][q][1];
+            }
         }
 }
 
-__global__ void __launch_bounds__(256) k_trinv_off(const double* __restrict__ L, double* __restrict__ X, int n, int d) {
-    __shared__ double A[CB][CB + 1][2], B[CB][CB + 1][2];
-    const int jb = blockIdx.x, ib = jb + d;
-    const int i0 = ib * CB, j0 = jb * CB;
-    const int ni = min(CB, n - i0), nj = min(CB, n - j0);
-    double tr[4] = {0, 0, 0, 0}, ti[4] = {0, 0, 0, 0};
-    for (int kb = jb; kb < ib; ++kb) {
-        const int k0 = kb * CB, nk = min(CB, n - k0);
-        for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-            const int r = e / CB, c = e % CB;
-            const bool ina = r < ni && c < nk, inb = r < nk && c < nj;
-            A[r][c][0] = ina ? L[((int64_t)(i0 + r) * n + k0 + c) * 2] : 0.0;
-            A[r][c][1] = ina ? L[((int64_t)(i0 + r) * n + k0 + c) * 2 + 1] : 0.0;
-            B[r][c][0] = inb ? X[((int64_t)(k0 + r) * n + j0 + c) * 2] : 0.0;
-            B[r][c][1] = inb ? X[((int64_t)(k0 + r) * n + j0 + c) * 2 + 1] : 0.0;
-        }
-        __syncthreads();
+// X_CA = -X_CC T_p; X_CC is lower triangular: only k < the end of the output
+// row tile contributes.  Grid (b/32, b/32, pairs).
+__global__ void __launch_bounds__(256) k_trinv_x(const double* __restrict__ T, double* __restrict__ X, int n, int b) {
+    __shared__ Tile32 t;
+    const int p = blockIdx.z, a0 = 2 * p * b, cc0 = a0 + b;
+    const int nc = min(b, n - cc0);
+    const int ti = blockIdx.y * CB, tj = blockIdx.x * CB;
+    if (ti >= nc) return;
+    const double* Tp = T + (int64_t)p * b * b * 2;
+    double acc[2][2][2] = {};
+    const int kend = min(nc, ti + CB);
+    for (int k0 = 0; k0 < kend; k0 += CB)
+        tile_mac(t, X, n, cc0 + ti, cc0 + k0, min(CB, nc - ti), min(CB, nc - k0), Tp, b, k0, tj, min(CB, nc - k0), CB,
+                 acc);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int o = threadIdx.x + 256 * q, r = o / CB, c = o % CB;
-            for (int k = 0; k < CB; ++k) {
-                tr[q] += A[r][k][0] * B[k][c][0] - A[r][k][1] * B[k][c][1];
-                ti[q] += A[r][k][0] * B[k][c][1] + A[r][k][1] * B[k][c][0];
+    for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = ti + ty + 16 * pp, c = tj + tx + 16 * q;
+            if (r < nc) {
+                X[((int64_t)(cc0 + r) * n + a0 + c) * 2] = -acc[pp][q][0];
+                X[((int64_t)(cc0 + r) * n + a0 + c) * 2 + 1] = -acc[pp][q][1];
             }
         }
-        __syncthreads();
-    }
-    // T into B, X_ii into A, then X_ij = -X_ii T
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int o = threadIdx.x + 256 * q, r = o / CB, c = o % CB;
-        B[r][c][0] = tr[q];
-        B[r][c][1] = ti[q];
-    }
-    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-        const int r = e / CB, c = e % CB;
-        const bool in = r < ni && c < ni;
-        A[r][c][0] = in ? X[((int64_t)(i0 + r) * n + i0 + c) * 2] : 0.0;
-        A[r][c][1] = in ? X[((int64_t)(i0 + r) * n + i0 + c) * 2 + 1] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int o = threadIdx.x + 256 * q, r = o / CB, c = o % CB;
-        double sr = 0.0, si = 0.0;
-        for (int k = 0; k < CB; ++k) {
-            sr += A[r][k][0] * B[k][c][0] - A[r][k][1] * B[k][c][1];
-            si += A[r][k][0] * B[k][c][1] + A[r][k][1] * B[k][c][0];
-        }
-        if (r < ni && c < nj) {
-            X[((int64_t)(i0 + r) * n + j0 + c) * 2] = -sr;
-            X[((int64_t)(i0 + r) * n + j0 + c) * 2 + 1] = -si;
-        }
-    }
 }
 
 }  // namespace
@@ -451,13 +492,10 @@ void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info) {
     const int n = d.desc.n_orb;
     MLMD_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), d.stream));
     const int nblk = (n + CB - 1) / CB;
+    double* Ld = (double*)d.mem.get((size_t)nblk * CB * CB * 2 * sizeof(double));
     for (int kb = 0; kb < nblk; ++kb) {
         const int below = n - (kb * CB + std::min(CB, n - kb * CB));
-        if (below > 0) {
-            k_chol_panel<<<(below + CB - 1) / CB, 256, 0, d.stream>>>(S, n, kb, d_info, 0);
-            d.launches++;
-        }
-        k_chol_panel<<<1, 256, 0, d.stream>>>(S, n, kb, d_info, 1);
+        k_chol_panel<<<std::max(1, (below + CB - 1) / CB), 256, 0, d.stream>>>(S, n, kb, Ld, d_info);
         d.launches++;
         if (below > 0) {
             const int t = (below + CB - 1) / CB;
@@ -465,19 +503,25 @@ void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info) {
             d.launches++;
         }
     }
-    // X = L^{-1} (blocked wavefront), then Minv = X^H
+    // X = L^{-1} by recursive doubling of inverted diagonal blocks, then Minv = X^H
     double* X = (double*)d.mem.get((size_t)n * n * 2 * sizeof(double));
+    double* T = (double*)d.mem.get((size_t)n * n * 2 * sizeof(double));
     MLMD_CUDA(cudaMemsetAsync(X, 0, (size_t)n * n * 2 * sizeof(double), d.stream));
-    k_trinv_diag<<<nblk, 32, 0, d.stream>>>(S, X, n);
+    k_trinv_diag<<<nblk, 256, 0, d.stream>>>(Ld, X, n);
     d.launches++;
-    for (int dd = 1; dd < nblk; ++dd) {
-        k_trinv_off<<<nblk - dd, 256, 0, d.stream>>>(S, X, n, dd);
-        d.launches++;
+    for (int b = CB; b < n; b *= 2) {
+        const int pairs = (n - b + 2 * b - 1) / (2 * b);      // pairs whose C block is non-empty
+        const dim3 grid(b / CB, b / CB, pairs);
+        k_trinv_t<<<grid, 256, 0, d.stream>>>(S, X, n, b, T);
+        k_trinv_x<<<grid, 256, 0, d.stream>>>(T, X, n, b);
+        d.launches += 2;
     }
     k_conj_transpose<<<(int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096), 256, 0, d.stream>>>(X, n, Minv);
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
+    d.mem.put(T);
     d.mem.put(X);
+    d.mem.put(Ld);
 }
 
 void lowdin_inverse_sqrt(Domain& d, double* S, double* Minv, double* work, int* d_info) {

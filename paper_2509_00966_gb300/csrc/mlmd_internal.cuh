@@ -232,6 +232,9 @@ void launch_overlap(Domain& d, const void* X, const void* Y, double scale, doubl
 bool launch_overlap_tc(Domain& d, const void* X, const void* Y, double scale, double* S);
 // Y[g][m] = sum_n X[g][n] M[n][m] (M complex double [n_orb][n_orb], device)
 void launch_update(Domain& d, const void* X, const double* M, void* Y);
+// Y = X M on the tensor cores in the domain's split mode (c64, non-FP32 GEMM
+// modes); false if the domain does not use them.
+bool launch_update_tc(Domain& d, const void* X, const double* M, void* Y);
 // In place: S -> lower Cholesky factor L (S = L L^H); returns false if S is
 // not positive definite.  Then Minv = L^{-H} (upper).
 void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info);

@@ -61,3 +61,28 @@ def test_reorth_through_tensor_core_gram(mode):
     assert np.max(np.abs(q - qr)) <= tol * np.abs(qr).max()
     assert np.max(np.abs(spec.dV * q.conj().T @ q - np.eye(40))) <= tol
     d.close()
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x2", "bf16x3", "fp16"])
+@pytest.mark.parametrize("n,n_orb,kind", [((12, 10, 14), 37, "chol"), ((24, 20, 16), 150, "chol"),
+                                          ((16, 16, 16), 80, "lowdin"), ((32, 32, 32), 256, "chol")])
+def test_reorth_update_tensor_cores(mode, n, n_orb, kind):
+    """Psi <- Psi M on the tensor cores (Y = X + X (M - I)) for nearly
+    orthonormal orbitals, ragged in grid points and orbital columns: the error
+    is that of the Gram matrix in the same mode (the update's own split error
+    scales with |M - I| ~ 1e-3)."""
+    spec = small_spec(precision="c64", n=n, n_orb=n_orb, steps=1)
+    d, V = gpu_domain(spec, gemm_mode=mode)
+    rng = np.random.default_rng(6)
+    psi = _orth(spec, 5)
+    psi = psi + 1e-3 * np.abs(psi).max() * (rng.standard_normal(psi.shape) + 1j * rng.standard_normal(psi.shape))
+    psi = psi.astype(np.complex64).astype(np.complex128)
+    d.set_orbitals(to_device(psi, "c64"))
+    d.reorthonormalize(kind)
+    q = to_numpy(d.get_orbitals())
+    qr = oracle.reorth(psi, spec.dV, kind)
+    err = np.max(np.abs(q - qr)) / np.abs(qr).max()
+    assert err <= 5 * TOL[mode], (mode, err)
+    orth = np.max(np.abs(spec.dV * q.conj().T @ q - np.eye(n_orb)))
+    assert orth <= 5 * TOL[mode], (mode, orth)
+    d.close()
