@@ -8,6 +8,9 @@
 #include <new>
 #include <vector>
 
+#include <map>
+#include <mutex>
+
 #include "mlmd_internal.cuh"
 
 using mlmd::Domain;
@@ -15,6 +18,19 @@ using mlmd::Error;
 
 
 namespace mlmd {
+
+void ensure_dynamic_smem(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> set;
+    int dev = 0;
+    MLMD_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = set[{dev, kernel}];
+    if (bytes > cur) {
+        MLMD_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        cur = bytes;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // allocator

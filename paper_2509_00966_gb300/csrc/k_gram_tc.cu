@@ -251,11 +251,7 @@ void gram_mode(Domain& d, const float* X, const float* Y, double scale, double* 
     nsplit = (nks + ks_per_split - 1) / ks_per_split;
     double* part = (double*)d.mem.get((size_t)nsplit * no * no * 2 * sizeof(double));
     constexpr uint32_t smem = STAGES * 2 * NPART * kTileBytes + 1024;
-    static bool attr = false;
-    if (!attr) {
-        MLMD_CUDA(cudaFuncSetAttribute(k_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    ensure_dynamic_smem(reinterpret_cast<const void*>(k_gram_tc<MODE>), smem);
     k_gram_tc<MODE><<<dim3(tiles, nsplit), 128, smem, d.stream>>>(pa, pb, nmt, nks, ks_per_split, no, same ? 1 : 0,
                                                                   unscale, part, d.err_flag);
     const int64_t nn = (int64_t)no * no;

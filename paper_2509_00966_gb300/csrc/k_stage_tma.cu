@@ -1,6 +1,6 @@
 // TMA-staged stage kernel: out = psi + gamma * h(A) w with the Hamiltonian
-// of Eq. 3, 2.5-D blocked, with the nonlocal term of Sec. V.B.5 fused on
-// both sides.
+// of Eq. 3, 2.5-D blocked, with the nonlocal scatter-back of Sec. V.B.5
+// fused, and the column projection kernel that prepares its input.
 //
 // A CTA owns an 8 x 8 tile of grid points in x-y, one 128-byte chunk of the
 // orbital row (16 complex64 or 8 complex128 orbitals; 64-byte chunks when the
@@ -13,11 +13,11 @@
 // thread's own points stay in registers as the window slides.
 //
 // Nonlocal part: the projections <b|w> of the atoms whose spheres touch the
-// column are staged in shared memory once per CTA (scatter-back B (D o P)),
-// and the projections of the output, <b|out>, are accumulated per column in
-// shared memory and added to the global result with one vector atomic per
-// (atom, projector, 16-byte vector) at the end; the next stage needs no
-// separate projection pass over the state.
+// column are staged in shared memory once per CTA for the scatter-back
+// B (D o P).  The projections of the output, <b|out>, which the next stage
+// needs, come from k_nl_project_cols over the same columns right after the
+// stage: summing them inside the plane loop put a reduction behind every
+// per-plane barrier, which cost more than reading the output once more.
 //
 // Every mbarrier wait is bounded: on expiry the CTA raises the domain's
 // error word, waits (bounded) for its copies in flight, and stops.
@@ -40,8 +40,9 @@ struct TmaMaps {
 struct TmaState {
     bool ok = false;          // tiles divide the grid and the row splits into chunks
     int vp = 0;               // 16-byte vectors per point per chunk (8 or 4)
+    int tpp = 4;              // threads per grid point of the stage kernel (4, or 8 with vp = 8)
     bool vp8_ok = false;      // the row splits into 128-byte chunks
-    bool tuned = false;       // chunk width chosen by timing
+    bool tuned = false;       // tile shape chosen by timing
     int zc = 0;               // planes per CTA
     int ncols = 0;            // tiles x z-chunks
     std::vector<TmaMaps> maps;
@@ -56,6 +57,7 @@ struct TmaState {
     int32_t* pe_off = nullptr;
     int32_t* pe_point = nullptr;
     void* pe_beta = nullptr;
+    int pcap = 0;             // most entries of one (column, plane), a multiple of 4
 };
 
 namespace {
@@ -169,7 +171,7 @@ template <typename R> struct TNl {
     // projection of the output, plane by plane: entries of (column, plane,
     // slot) in pe_off[((col * zc + iz) * (maxs + 1)) + s .. + s + 1]
     const int32_t* pe_off;
-    const int32_t* pe_point;   // local point index (y * 8 + x) within the tile
+    const int32_t* pe_point;   // key: local point index (y * 8 + x) within the tile | slot << 8
     const R* pe_beta;          // [..][NP]
     R dV;
     int maxs;                  // staging capacity (atoms per column)
@@ -196,29 +198,28 @@ __device__ __forceinline__ void global_add(double* p, float4 v, double s) {
     atomicAdd(p + 1, s * d.y);
 }
 
-template <typename R, int ORDER, int VP, int NP, int NSLOT>
-__global__ void __launch_bounds__(256, 2)
+template <typename R, int ORDER, int VP, int NP, int NSLOT, int TPP>
+__global__ void __launch_bounds__(64 * TPP, 2)
     k_stage_tma(const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_x,
                 const __grid_constant__ CUtensorMap tm_y, TGeo<R> G, const R* psi, R* out,
                 const R* __restrict__ V, const R* __restrict__ f, const double* __restrict__ Ak, TNl<R> N,
                 R gre, R gim, double* __restrict__ obs, int* err) {
     constexpr int NC = V16<R>::NC;
-    constexpr int NVT = VP / 4;                     // 16-byte vectors of its point per thread
+    constexpr int NVT = VP / TPP;                   // 16-byte vectors of its point per thread
+    constexpr int NT = 64 * TPP;                    // threads
     constexpr int OCR = VP * 16 / sizeof(R);        // reals per chunk row
     constexpr int NPV = (NP > 0 ? NP : 1);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations on a 128-byte boundary (the launch adds 128 bytes of slack)
     float4* ring = reinterpret_cast<float4*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     float4* sP = ring + NSLOT * Slot<VP>::N;        // [maxs][NP][VP] staged <b|w>
-    float4* sAcc = sP + N.maxs * NPV * VP;          // [maxs][NP][VP] accumulated <b|out>
-    float4* sO = sAcc + N.maxs * NPV * VP;          // [2][64][VP] outputs of the last two planes
-    R* sD = reinterpret_cast<R*>(sO + (NP > 0 ? 2 * 64 * VP : 0));   // [maxs][NP]
+    R* sD = reinterpret_cast<R*>(sP + N.maxs * NPV * VP);   // [maxs][NP]
     __shared__ __align__(8) uint64_t bars[NSLOT];
     __shared__ R sA[4];
     __shared__ int abort_sh;
 
     const int tid = threadIdx.x;
-    const int pt = tid >> 2, jv = tid & 3;          // point of the tile, first vector (then jv + 4k)
+    const int pt = tid / TPP, jv = tid % TPP;       // point of the tile, first vector (then jv + TPP k)
     const int lx = pt % TX, ly = pt / TX;
     const int tile = blockIdx.x;
     const int x0 = (tile % G.ntx) * TX, y0 = (tile / G.ntx) * TY;
@@ -229,7 +230,6 @@ __global__ void __launch_bounds__(256, 2)
     const int c0 = chunk * OCR;                     // first real of the chunk within a row
     const bool has_psi = psi != nullptr;
     const bool do_obs = obs != nullptr;
-    const bool proj = NP > 0 && N.Pout != nullptr;
     const int col = blockIdx.x + gridDim.x * blockIdx.z;
 
     if (tid == 0) {
@@ -243,13 +243,12 @@ __global__ void __launch_bounds__(256, 2)
     if (NP > 0) {
         cs = N.col_start[col];
         na = N.col_start[col + 1] - cs;
-        for (int idx = tid; idx < na * NPV * VP; idx += 256) {
+        for (int idx = tid; idx < na * NPV * VP; idx += NT) {
             const int s = idx / (NPV * VP), r = idx - s * (NPV * VP), i = r / VP, jj = r - i * VP;
             const int64_t a = N.col_atom[cs + s];
             sP[idx] = __ldg(reinterpret_cast<const float4*>(N.Pin + (a * NPV + i) * 2 * G.ld + c0) + jj);
-            sAcc[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int idx = tid; idx < na * NPV; idx += 256) {
+        for (int idx = tid; idx < na * NPV; idx += NT) {
             const int s = idx / NPV, i = idx - s * NPV;
             sD[idx] = N.D[(int64_t)N.col_atom[cs + s] * NPV + i];
         }
@@ -296,7 +295,7 @@ __global__ void __launch_bounds__(256, 2)
         for (int p = 0; p < 4; ++p) {
             const float4* s = ring + (p % NSLOT) * Slot<VP>::N;
 #pragma unroll
-            for (int k = 0; k < NVT; ++k) unpack(s[offC + 4 * k], q[k][p]);
+            for (int k = 0; k < NVT; ++k) unpack(s[offC + TPP * k], q[k][p]);
         }
     }
     if (tid == 0) waited = aborted0 ? 0 : 4;
@@ -307,64 +306,13 @@ __global__ void __launch_bounds__(256, 2)
         ++issued;
     }
 
-    // <b|out> of plane iz (outputs in sO[iz & 1]).  Warp w owns the atom
-    // slots s = w, w + 8, ...; its lanes split the 16-byte vectors (VP of
-    // them) and the slot's entries (32 / VP groups), reduce across the entry
-    // groups with shuffles, and one group updates the warp-owned
-    // accumulators, so no two warps touch the same accumulator.
-    auto project_plane = [&](int iz) {
-        constexpr int NEG = 32 / VP;
-        const int lane = tid & 31, warp = tid >> 5;
-        const int jj = lane % VP, eg = lane / VP;
-        const float4* so = sO + (iz & 1) * 64 * VP;
-        const int32_t* po = N.pe_off + ((int64_t)col * G.zc + iz) * (N.maxs + 1);
-        for (int s = warp; s < na; s += 8) {
-            const int e0 = po[s], e1 = po[s + 1];
-            Cv<R> a[NPV];
-#pragma unroll
-            for (int pi = 0; pi < NPV; ++pi)
-#pragma unroll
-                for (int u = 0; u < NC; ++u) { a[pi].re[u] = 0; a[pi].im[u] = 0; }
-            for (int e = e0 + eg; e < e1; e += NEG) {
-                R b[NPV];
-                load_beta<R, NPV>(N.pe_beta + (int64_t)e * NPV, b);
-                Cv<R> ov;
-                unpack(so[N.pe_point[e] * VP + jj], ov);
-#pragma unroll
-                for (int pi = 0; pi < NPV; ++pi)
-#pragma unroll
-                    for (int u = 0; u < NC; ++u) {
-                        a[pi].re[u] += b[pi] * ov.re[u];
-                        a[pi].im[u] += b[pi] * ov.im[u];
-                    }
-            }
-#pragma unroll
-            for (int off = VP; off < 32; off <<= 1)
-#pragma unroll
-                for (int pi = 0; pi < NPV; ++pi)
-#pragma unroll
-                    for (int u = 0; u < NC; ++u) {
-                        a[pi].re[u] += __shfl_xor_sync(0xffffffffu, a[pi].re[u], off);
-                        a[pi].im[u] += __shfl_xor_sync(0xffffffffu, a[pi].im[u], off);
-                    }
-            if (eg == 0) {
-#pragma unroll
-                for (int pi = 0; pi < NPV; ++pi) {
-                    float4* dst = &sAcc[(s * NPV + pi) * VP + jj];
-                    Cv<R> av;
-                    unpack(*dst, av);
-#pragma unroll
-                    for (int u = 0; u < NC; ++u) { av.re[u] += a[pi].re[u]; av.im[u] += a[pi].im[u]; }
-                    *dst = pack(av);
-                }
-            }
-        }
-    };
-
     R acc[5] = {0, 0, 0, 0, 0};
     const int64_t plane_stride = (int64_t)G.nx * G.ny;
     int64_t g = (x0 + lx) + (int64_t)G.nx * (y0 + ly) + plane_stride * z0;
     const int64_t row = 2 * (int64_t)G.ld;
+    // nonlocal entry range of this thread's point, one plane ahead
+    int e0n = 0, e1n = 0;
+    if (NP > 0 && nzc > 0) { e0n = N.pstart[g]; e1n = N.pstart[g + 1]; }
     for (int i = 0; i < nzc && !aborted0; ++i, g += plane_stride) {
         // per-point global loads first, so that they overlap the plane wait
         // and the shared-memory stencil
@@ -372,9 +320,17 @@ __global__ void __launch_bounds__(256, 2)
         float4 pp[NVT];
         if (has_psi)
 #pragma unroll
-            for (int k = 0; k < NVT; ++k) pp[k] = *(reinterpret_cast<const float4*>(psi + g * row + c0) + jv + 4 * k);
-        int e0 = 0, e1 = 0;
-        if (NP > 0) { e0 = N.pstart[g]; e1 = N.pstart[g + 1]; }
+            for (int k = 0; k < NVT; ++k) pp[k] = *(reinterpret_cast<const float4*>(psi + g * row + c0) + jv + TPP * k);
+        const int e0 = e0n, e1 = e1n;
+        int sf = 0;
+        R bf[NPV];
+        if (NP > 0) {
+            if (i + 1 < nzc) { e0n = N.pstart[g + plane_stride]; e1n = N.pstart[g + plane_stride + 1]; }
+            if (e0 < e1) {      // the first entry's slot and beta * D
+                sf = N.slot[e0];
+                load_beta<R, NPV>(N.beta + (int64_t)e0 * NPV, bf);
+            }
+        }
         // plane z+2 (p = i+4) must have landed
         ok = wait_plane(i + 4);
         if (!ok) abort_sh = 1;
@@ -388,24 +344,23 @@ __global__ void __launch_bounds__(256, 2)
                 ++issued;
             }
         }
-        if (proj && i > 0) project_plane(i - 1);   // its outputs were written before barrier A
         const float4* sc = ring + ((i + 2) % NSLOT) * Slot<VP>::N;    // plane z
         const float4* s4 = ring + ((i + 4) % NSLOT) * Slot<VP>::N;    // plane z+2
         Cv<R> hw[NVT], dd[NVT][3];
 #pragma unroll
         for (int k = 0; k < NVT; ++k) {
-            unpack(s4[offC + 4 * k], q[k][4]);
+            unpack(s4[offC + TPP * k], q[k][4]);
             const Cv<R>& c = q[k][2];
             Cv<R> lap, t1, t2, t3, t4;
 #pragma unroll
             for (int e = 0; e < NC; ++e) { lap.re[e] = G.kc0 * c.re[e]; lap.im[e] = G.kc0 * c.im[e]; }
 #pragma unroll
             for (int ax = 0; ax < 2; ++ax) {
-                unpack(sc[offN[2 * ax] + 4 * k], t1);
-                unpack(sc[offN[2 * ax + 1] + 4 * k], t2);
+                unpack(sc[offN[2 * ax] + TPP * k], t1);
+                unpack(sc[offN[2 * ax + 1] + TPP * k], t2);
                 if (ORDER == 4) {
-                    unpack(sc[offN[4 + 2 * ax] + 4 * k], t3);
-                    unpack(sc[offN[5 + 2 * ax] + 4 * k], t4);
+                    unpack(sc[offN[4 + 2 * ax] + TPP * k], t3);
+                    unpack(sc[offN[5 + 2 * ax] + TPP * k], t4);
                 }
 #pragma unroll
                 for (int e = 0; e < NC; ++e) {
@@ -445,16 +400,22 @@ __global__ void __launch_bounds__(256, 2)
         }
         if (NP > 0) {           // scatter-back: sum_(a,i) b_ai(r) D_ai <b_ai|w>
             for (int e = e0; e < e1; ++e) {
-                const int s = N.slot[e];
+                int s = sf;
                 R b[NPV];
-                load_beta<R, NPV>(N.beta + (int64_t)e * NPV, b);   // beta * D
+                if (e == e0) {
+#pragma unroll
+                    for (int pi = 0; pi < NPV; ++pi) b[pi] = bf[pi];
+                } else {
+                    s = N.slot[e];
+                    load_beta<R, NPV>(N.beta + (int64_t)e * NPV, b);   // beta * D
+                }
 #pragma unroll
                 for (int pi = 0; pi < NPV; ++pi) {
                     const R bd = b[pi];
 #pragma unroll
                     for (int k = 0; k < NVT; ++k) {
                         Cv<R> pv;
-                        unpack(sP[(s * NPV + pi) * VP + jv + 4 * k], pv);
+                        unpack(sP[(s * NPV + pi) * VP + jv + TPP * k], pv);
 #pragma unroll
                         for (int u = 0; u < NC; ++u) {
                             hw[k].re[u] += bd * pv.re[u];
@@ -483,13 +444,12 @@ __global__ void __launch_bounds__(256, 2)
                 }
             }
             const float4 ov = pack(o);
-            *(reinterpret_cast<float4*>(out + g * row + c0) + jv + 4 * k) = ov;
-            if (proj) sO[(i & 1) * 64 * VP + pt * VP + jv + 4 * k] = ov;
+            *(reinterpret_cast<float4*>(out + g * row + c0) + jv + TPP * k) = ov;
             if (do_obs) {
                 const Cv<R>& c = q[k][2];
 #pragma unroll
                 for (int e = 0; e < NC; ++e) {
-                    const R fo = f[c0 / 2 + (jv + 4 * k) * NC + e];
+                    const R fo = f[c0 / 2 + (jv + TPP * k) * NC + e];
                     const R cr = c.re[e], ci = c.im[e];
                     acc[0] += fo * (cr * cr + ci * ci);
                     acc[1] += fo * (cr * hw[k].re[e] + ci * hw[k].im[e]);
@@ -508,19 +468,8 @@ __global__ void __launch_bounds__(256, 2)
             for (int p = waited; p < issued; ++p) (void)wait_plane(p);
         }
     }
-    if (proj) {
-        __syncthreads();
-        if (!abort_sh && nzc > 0) project_plane(nzc - 1);
-        __syncthreads();
-        if (!abort_sh)
-            for (int idx = tid; idx < na * NPV * VP; idx += 256) {
-                const int s = idx / (NPV * VP), r = idx - s * (NPV * VP), i = r / VP, jj = r - i * VP;
-                const int64_t a = N.col_atom[cs + s];
-                global_add(N.Pout + (a * NPV + i) * 2 * G.ld + c0 + jj * (16 / (int)sizeof(R)), sAcc[idx], N.dV);
-            }
-    }
     if (do_obs) {
-        __shared__ double sh[8][5];
+        __shared__ double sh[NT / 32][5];
         const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
         for (int v = 0; v < 5; ++v)
@@ -531,13 +480,167 @@ __global__ void __launch_bounds__(256, 2)
         __syncthreads();
         if (tid < 5) {
             double t = 0.0;
-            for (int w = 0; w < 8; ++w) t += sh[w][tid];
+            for (int w = 0; w < NT / 32; ++w) t += sh[w][tid];
             const int64_t blin = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
             obs[blin * 5 + tid] = t;
         }
     }
 }
 
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// <b|W> for every atom, column by column (the stage kernel's columns and
+// tables).  Thread 0 streams, per plane of the column, the 8 x 8 tile of W's
+// chunk (one TMA) and the plane's entries -- key = point | slot << 8, sorted
+// by slot, and beta -- (two bulk copies) into a ring of NBUF buffers.  The
+// plane's entries are cut into eight equal runs, one per warp, whatever
+// slot they belong to, so the warps share the work evenly even when one atom
+// fills the column and another only grazes it.  Lane (projector, vector)
+// sums beta * W along its warp's run in registers and flushes the sum into
+// the column's accumulator sAcc[slot][projector][vector] (shared-memory
+// atomics) when the run passes to the next slot; at the end every
+// accumulator goes to Pout with one vector atomic.
+template <typename R, int VP, int NP>
+__global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__ CUtensorMap tm_c, TNl<R> N, int nx,
+                                                         int ny, int nz, int ntx, int zc, int ld, int pcap,
+                                                         int* err) {
+    constexpr int NBUF = 4;
+    constexpr int OCR = VP * 16 / sizeof(R);
+    constexpr int NC = V16<R>::NC;
+    constexpr int PPW = 32 / VP;                    // projectors per warp pass
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    // buffer b: W tile [64][VP] float4, then keys [pcap + 8] int32, then beta [pcap][NP] R;
+    // after the NBUF buffers: sAcc [maxs][NP][VP] float4
+    const uint32_t wbytes = 64 * VP * 16;
+    const uint32_t pbytes = (uint32_t)(pcap + 8) * 4;
+    const uint32_t bbytes = (uint32_t)pcap * NP * sizeof(R);
+    const uint32_t bufbytes = (wbytes + pbytes + bbytes + 127) / 128 * 128;
+    float4* sAcc = reinterpret_cast<float4*>(base + NBUF * bufbytes);
+    __shared__ __align__(8) uint64_t bars[NBUF];
+    __shared__ int abort_sh;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int col = blockIdx.x + gridDim.x * blockIdx.z;
+    const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
+    const int z0 = blockIdx.z * zc;
+    const int nzc = min(zc, nz - z0);
+    const int c0 = blockIdx.y * OCR;
+    const int cs = N.col_start[col], na = N.col_start[col + 1] - cs;
+    const int stride = N.maxs + 1;
+    if (tid == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+        abort_sh = 0;
+        fence_proxy_async();
+    }
+    for (int i = tid; i < na * NP * VP; i += 256) sAcc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    if (na == 0) return;
+
+    auto issue = [&](int iz) {      // plane iz of the column into buffer iz % NBUF
+        unsigned char* buf = base + (iz % NBUF) * bufbytes;
+        const int32_t* po = N.pe_off + ((int64_t)col * zc + iz) * stride;
+        const int b0 = po[0], b1 = po[na];
+        const int a0 = b0 & ~3, a1 = (b1 + 3) & ~3;
+        uint32_t bytes = wbytes;
+        if (b1 > b0) bytes += (uint32_t)(a1 - a0) * 4 + (uint32_t)(b1 - b0) * NP * sizeof(R);
+        mbar_expect_tx(&bars[iz % NBUF], bytes);
+        tma_load_4d(buf, &tm_c, c0, x0, y0, z0 + iz, &bars[iz % NBUF]);
+        if (b1 > b0) {
+            bulk_g2s(buf + wbytes, N.pe_point + a0, (uint32_t)(a1 - a0) * 4, &bars[iz % NBUF]);
+            bulk_g2s(buf + wbytes + pbytes, N.pe_beta + (int64_t)b0 * NP, (uint32_t)(b1 - b0) * NP * sizeof(R),
+                     &bars[iz % NBUF]);
+        }
+    };
+    int issued = 0;
+    if (tid == 0) {
+        for (; issued < NBUF && issued < nzc; ++issued) issue(issued);
+    }
+
+    const int jj = lane % VP, pl = lane / VP;
+    auto flush = [&](int s, int pi, const Cv<R>& a) {
+        R* dst = reinterpret_cast<R*>(&sAcc[(s * NP + pi) * VP + jj]);
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+            atomicAdd(dst + 2 * u, a.re[u]);
+            atomicAdd(dst + 2 * u + 1, a.im[u]);
+        }
+    };
+    int waited = 0;
+    for (int iz = 0; iz < nzc; ++iz) {
+        const bool ok = mbar_wait_bounded(&bars[iz % NBUF], (uint32_t)((iz / NBUF) & 1));
+        if (!ok) abort_sh = 1;
+        if (tid == 0) waited = iz + 1;
+        const unsigned char* buf = base + (iz % NBUF) * bufbytes;
+        const float4* sW = reinterpret_cast<const float4*>(buf);
+        const int32_t* po = N.pe_off + ((int64_t)col * zc + iz) * stride;
+        const int b0 = po[0], b1 = po[na], a0 = b0 & ~3;
+        const int32_t* sKey = reinterpret_cast<const int32_t*>(buf + wbytes) - a0;
+        const R* sB = reinterpret_cast<const R*>(buf + wbytes + pbytes) - (int64_t)b0 * NP;
+        // this warp's run of the plane's entries
+        const int T = b1 - b0;
+        const int r0 = b0 + (int)(((int64_t)T * warp) / 8), r1 = b0 + (int)(((int64_t)T * (warp + 1)) / 8);
+        if (ok && r1 > r0) {
+#pragma unroll
+            for (int pg = 0; pg < (NP + PPW - 1) / PPW; ++pg) {
+                const int pi = pg * PPW + pl;
+                if (pi < NP) {
+                    int cur = sKey[r0] >> 8;
+                    Cv<R> a;
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) { a.re[u] = 0; a.im[u] = 0; }
+                    for (int e = r0; e < r1; ++e) {
+                        const int key = sKey[e], s = key >> 8;
+                        if (s != cur) {
+                            flush(cur, pi, a);
+#pragma unroll
+                            for (int u = 0; u < NC; ++u) { a.re[u] = 0; a.im[u] = 0; }
+                            cur = s;
+                        }
+                        const R bv = sB[(int64_t)e * NP + pi];
+                        Cv<R> w;
+                        unpack(sW[(key & 63) * VP + jj], w);
+#pragma unroll
+                        for (int u = 0; u < NC; ++u) { a.re[u] += bv * w.re[u]; a.im[u] += bv * w.im[u]; }
+                    }
+                    flush(cur, pi, a);
+                }
+            }
+        }
+        __syncthreads();                    // buffer iz % NBUF is free again
+        if (abort_sh) break;
+        if (tid == 0 && issued < nzc) {
+            fence_proxy_async();
+            issue(issued);
+            ++issued;
+        }
+    }
+    if (abort_sh) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int iz = waited; iz < issued; ++iz) (void)mbar_wait_bounded(&bars[iz % NBUF], (uint32_t)((iz / NBUF) & 1));
+        }
+        return;
+    }
+    __syncthreads();
+    const int64_t row = 2 * (int64_t)ld;
+    for (int i = tid; i < na * NP * VP; i += 256) {
+        const int s = i / (NP * VP), r = i - s * (NP * VP), pi = r / VP, j = r - pi * VP;
+        const int64_t a = N.col_atom[cs + s];
+        global_add(N.Pout + (a * NP + pi) * row + c0 + j * (16 / (int)sizeof(R)), sAcc[i], N.dV);
+    }
+}
+
+template <typename R, int VP>
+size_t project_smem(int np, int pcap, int maxs) {
+    const size_t w = 64 * VP * 16, p = (size_t)(pcap + 8) * 4, b = (size_t)pcap * np * sizeof(R);
+    return 4 * ((w + p + b + 127) / 128 * 128) + (size_t)maxs * np * VP * 16 + 128;
+}
 
 // ---------------------------------------------------------------------------
 // host side
@@ -550,9 +653,11 @@ size_t smem_bytes(int maxs) {
     const int npv = NP > 0 ? NP : 1;
     size_t b = (size_t)NSLOT * Slot<VP>::BYTES;
     if (NP > 0)
-        b += 2 * (size_t)maxs * npv * VP * 16 + 2 * 64 * VP * 16 + ((size_t)maxs * npv * sizeof(R) + 15) / 16 * 16;
+        b += (size_t)maxs * npv * VP * 16 + ((size_t)maxs * npv * sizeof(R) + 15) / 16 * 16;
     return b + 128;
 }
+
+TmaMaps maps_for(Domain& d, const void* base);
 
 template <typename R, int ORDER, int VP, int NP>
 void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool proj) {
@@ -581,16 +686,29 @@ void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool
         N.maxs = t.maxs;
     }
     const size_t smem = smem_bytes<R, VP, NP>(NP > 0 ? t.maxs : 0);
-    auto kern = k_stage_tma<R, ORDER, VP, NP, NSLOT>;
-    static size_t attr_bytes = 0;
-    if (smem > attr_bytes) {
-        MLMD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_bytes = smem;
+    constexpr int TPP_WIDE = VP == 8 ? 8 : 4;       // one 16-byte vector per thread
+    const int tpp = t.tpp == 8 ? TPP_WIDE : 4;
+    auto kern = tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, NSLOT, TPP_WIDE> : k_stage_tma<R, ORDER, VP, NP, NSLOT, 4>;
+    ensure_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
+    N.Pout = nullptr;
+    {
+        ProfScope ps(d.prof, MLMD_KERNEL_STAGE, d.stream);
+        kern<<<grid, 64 * tpp, smem, d.stream>>>(m.centre, m.xslab, m.yslab, G, static_cast<const R*>(a.psi),
+                                           static_cast<R*>(a.out), static_cast<const R*>(d.V),
+                                           static_cast<const R*>(d.fR), a.A, N, (R)a.gamma_re, (R)a.gamma_im, a.obs,
+                                           d.err_flag);
     }
-    kern<<<grid, 256, smem, d.stream>>>(m.centre, m.xslab, m.yslab, G, static_cast<const R*>(a.psi),
-                                       static_cast<R*>(a.out), static_cast<const R*>(d.V),
-                                       static_cast<const R*>(d.fR), a.A, N, (R)a.gamma_re, (R)a.gamma_im, a.obs,
-                                       d.err_flag);
+    if constexpr (NP > 0) {
+        if (!proj) return;
+        N.Pout = static_cast<R*>(a.P_out);
+        const TmaMaps mo = maps_for(d, a.out);
+        const size_t psm = project_smem<R, VP>(NP, t.pcap, t.maxs);
+        auto pk = k_nl_project_cols<R, VP, NP>;
+        ensure_dynamic_smem(reinterpret_cast<const void*>(pk), psm);
+        ProfScope ps(d.prof, MLMD_KERNEL_PROJECT, d.stream);
+        pk<<<grid, 256, psm, d.stream>>>(mo.centre, N, G.nx, G.ny, G.nz, G.ntx, G.zc, G.ld, t.pcap, d.err_flag);
+        d.launches++;
+    }
 }
 
 template <typename R, int VP, int NP>
@@ -659,7 +777,7 @@ void tma_setup(Domain& d) {
     t.vp8_ok = row_bytes % 128 == 0;
     t.vp = t.vp8_ok ? 8 : ((row_bytes % 64 == 0 && d.c64()) ? 4 : 0);
     t.ok = t.vp != 0 && nx % TX == 0 && ny % TY == 0 && std::getenv("MLMD_NO_TMA") == nullptr;
-    t.tuned = !(t.vp8_ok && d.c64());      // complex128 rows: 128-byte chunks only
+    t.tuned = false;
     if (!t.ok) return;
     // z range per CTA: enough CTAs to fill the GPU, at most 16 planes (fewer
     // atoms per column keep the staged projections small)
@@ -762,22 +880,31 @@ void tma_build_nl(Domain& d, const double* D_host) {
             const int64_t g = idx[q];
             const int64_t k = key_of(g, qslot[q]);
             const int64_t e = pst[k] + pcur[k]++;
-            pe_point[e] = (int32_t)((((g / nx) % ny) % TY) * TX + (g % nx) % TX);
+            pe_point[e] = (int32_t)((((g / nx) % ny) % TY) * TX + (g % nx) % TX) | (qslot[q] << 8);
             for (int i = 0; i < np; ++i) {
                 if (rs == 4) reinterpret_cast<float*>(pe_beta.data())[e * np + i] = (float)beta[q * np + i];
                 else reinterpret_cast<double*>(pe_beta.data())[e * np + i] = beta[q * np + i];
             }
         }
+    // most entries of one (column, plane): the projection kernel's buffers
+    int pcap = 0;
+    for (int64_t gr = 0; gr < ngrp; ++gr) pcap = std::max(pcap, pe_off[gr * (M + 1) + M] - pe_off[gr * (M + 1)]);
+    t.pcap = (pcap + 3) / 4 * 4;
+    pe_point.resize(pe_point.size() + 8, 0);        // slack for copies rounded out to 16 bytes
     size_t sm8 = 0, sm4 = 0;
     if (d.c64()) {
-        sm8 = np == 4 ? smem_bytes<float, 8, 4>(t.maxs) : smem_bytes<float, 8, 8>(t.maxs);
-        sm4 = np == 4 ? smem_bytes<float, 4, 4>(t.maxs) : smem_bytes<float, 4, 8>(t.maxs);
+        sm8 = std::max(np == 4 ? smem_bytes<float, 8, 4>(t.maxs) : smem_bytes<float, 8, 8>(t.maxs),
+                       project_smem<float, 8>(np, t.pcap, t.maxs));
+        sm4 = std::max(np == 4 ? smem_bytes<float, 4, 4>(t.maxs) : smem_bytes<float, 4, 8>(t.maxs),
+                       project_smem<float, 4>(np, t.pcap, t.maxs));
     } else {
-        sm8 = sm4 = np == 4 ? smem_bytes<double, 8, 4>(t.maxs) : smem_bytes<double, 8, 8>(t.maxs);
+        sm8 = sm4 = std::max(np == 4 ? smem_bytes<double, 8, 4>(t.maxs) : smem_bytes<double, 8, 8>(t.maxs),
+                             project_smem<double, 8>(np, t.pcap, t.maxs));
     }
     const size_t kMaxSmem = 200 * 1024;
     if (sm4 > kMaxSmem) return;   // too many atoms per column for the staging: plain kernel
-    if (t.vp == 8 && sm8 > kMaxSmem) {
+    if (t.vp == 8 && (sm8 > kMaxSmem || !d.c64())) {
+        if (!d.c64()) return;
         t.vp = 4;                 // only the narrower chunks fit
         t.vp8_ok = false;
         t.maps.clear();
@@ -821,7 +948,6 @@ bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done) {
     dim3 grid((d.desc.n[0] / TX) * (d.desc.n[1] / TY), chunks_of(d), (d.desc.n[2] + t.zc - 1) / t.zc);
     if (proj)
         MLMD_CUDA(cudaMemsetAsync(a.P_out, 0, (size_t)d.nl.n_atoms * d.nl.n_proj * d.ld * d.elem, d.stream));
-    ProfScope ps(d.prof, MLMD_KERNEL_STAGE, d.stream);
     if (d.c64()) {
         if (t.vp == 8) tma_np<float, 8>(d, a, m, grid, nl, proj);
         else tma_np<float, 4>(d, a, m, grid, nl, proj);
@@ -834,17 +960,24 @@ bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done) {
     return true;
 }
 
-// Pick the orbital-chunk width (128- or 64-byte rows per CTA) of the TMA
-// stage kernel by timing a few launches of each on the domain's own data.
+// Pick the tile shape of the TMA stage kernel -- orbital-chunk width (128- or
+// 64-byte rows per CTA) and threads per grid point (4, or 8 with 128-byte
+// chunks) -- by timing a few launches of each on the domain's own data.
 // The timed launches read psi and write only the work buffer wb and the
 // projection buffer Pb, which every step overwrites before reading.
 void tma_autotune(Domain& d, const double* Ak) {
     if (!d.tma || !d.tma->ok || d.tma->tuned) return;
     TmaState& t = *d.tma;
     t.tuned = true;
-    if (!t.vp8_ok || !d.c64()) return;
     const bool nl = d.has_nl();
     if (nl && !t.nl_ok) return;
+    std::vector<std::pair<int, int>> cand;
+    if (t.vp == 8) {
+        cand.push_back({8, 4});
+        cand.push_back({8, 8});
+    }
+    if (d.c64() && (t.vp == 4 || t.vp8_ok)) cand.push_back({4, 4});
+    if (cand.size() < 2) return;
     StageArgs a;
     a.w = d.psi;
     a.psi = d.psi;
@@ -858,9 +991,10 @@ void tma_autotune(Domain& d, const double* Ak) {
     MLMD_CUDA(cudaEventCreate(&e0));
     MLMD_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_vp = t.vp;
-    for (int vp : {8, 4}) {
-        t.vp = vp;
+    std::pair<int, int> pick = cand[0];
+    for (const auto& c : cand) {
+        t.vp = c.first;
+        t.tpp = c.second;
         t.maps.clear();
         launch_stage_tma(d, a, nullptr);      // warm-up (also sets the kernel attribute)
         MLMD_CUDA(cudaEventRecord(e0, d.stream));
@@ -869,11 +1003,12 @@ void tma_autotune(Domain& d, const double* Ak) {
         MLMD_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         MLMD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; best_vp = vp; }
+        if (ms < best) { best = ms; pick = c; }
     }
     (void)cudaEventDestroy(e0);
     (void)cudaEventDestroy(e1);
-    t.vp = best_vp;
+    t.vp = pick.first;
+    t.tpp = pick.second;
     t.maps.clear();
 }
 

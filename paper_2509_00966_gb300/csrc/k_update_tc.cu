@@ -288,11 +288,7 @@ void update_mode(Domain& d, const float* X, const double* M, float* Y) {
     k_split_embed<MODE><<<dim3(nkt, njt), 256, 0, d.stream>>>(M, n, njt, nkt, maxbits, pb);
     d.launches += 2;
     constexpr uint32_t smem = STAGES * 2 * NPART * kTileBytes + 1024;
-    static bool attr = false;
-    if (!attr) {
-        MLMD_CUDA(cudaFuncSetAttribute(k_update_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    ensure_dynamic_smem(reinterpret_cast<const void*>(k_update_tc<MODE>), smem);
     k_update_tc<MODE><<<dim3(njt, ngt), 128, smem, d.stream>>>(pa, pb, ngt, njt, nkt, X, Y, d.ng, ncols, xunscale,
                                                                maxbits, d.err_flag);
     d.launches++;

@@ -23,7 +23,8 @@ struct Error {
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \
         if (e_ != cudaSuccess)                                                               \
-            throw ::mlmd::Error{MLMD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+            throw ::mlmd::Error{MLMD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + \
+                                " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"};                \
     } while (0)
 
 #define MLMD_REQUIRE(cond, code, text)                                      \
@@ -180,6 +181,11 @@ int launch_stage(Domain& d, const StageArgs& a, bool* proj_done = nullptr);
 int stage_blocks(const Domain& d);
 
 Geo geo_of(const Domain& d);
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The attribute belongs to the kernel function on each
+// device, not to a launch site, so the cache is keyed by (device, kernel).
+void ensure_dynamic_smem(const void* kernel, size_t bytes);
 
 // TMA-staged stage kernel (k_stage_tma.cu): set up at domain creation; the
 // launch returns false when the grid or row does not tile (then the plain
