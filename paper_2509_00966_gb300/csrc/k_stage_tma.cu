@@ -54,10 +54,14 @@ struct TmaState {
     int32_t* ent_slot = nullptr;
     void* ent_beta = nullptr;
     void* D = nullptr;
-    int32_t* pe_off = nullptr;
-    int32_t* pe_point = nullptr;
-    void* pe_beta = nullptr;
-    int pcap = 0;             // most entries of one (column, plane), a multiple of 4
+    // projection tables: half-height columns of PZC planes, entries slot-major
+    int pzc = 0;              // planes per projection column
+    int pcap = 0;             // most entries of one projection column, a multiple of 4
+    int32_t* pp_seg = nullptr;        // [slots + 1] first entry of each (column, slot)
+    int32_t* pp_atom_start = nullptr; // [ncols_p + 1] ranges of pp_atom
+    int32_t* pp_atom = nullptr;       // atoms of each projection column, ascending
+    int32_t* pp_key = nullptr;        // [n_list + 8] point | plane << 6 | slot << 10
+    void* pp_beta = nullptr;          // [n_list][NP]
 };
 
 namespace {
@@ -168,11 +172,13 @@ template <typename R> struct TNl {
     const R* D;                // [n_atoms][NP]
     const R* Pin;              // <b|w>: [n_atoms][NP] rows of 2 ld reals
     R* Pout;                   // <b|out> accumulated (zeroed by the caller), or null
-    // projection of the output, plane by plane: entries of (column, plane,
-    // slot) in pe_off[((col * zc + iz) * (maxs + 1)) + s .. + s + 1]
-    const int32_t* pe_off;
-    const int32_t* pe_point;   // key: local point index (y * 8 + x) within the tile | slot << 8
-    const R* pe_beta;          // [..][NP]
+    // projection of the output: projection columns (PZC planes), entries
+    // ordered by (slot, plane, point) within a column
+    const int32_t* pp_seg;     // [slots + 1] first entry of each (column, slot)
+    const int32_t* pp_atom_start;
+    const int32_t* pp_atom;
+    const int32_t* pp_key;     // W row in the column's planes: plane * 64 + y * 8 + x
+    const R* pp_beta;          // [..][NP]
     R dV;
     int maxs;                  // staging capacity (atoms per column)
 };
@@ -494,152 +500,109 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
-// <b|W> for every atom, column by column (the stage kernel's columns and
-// tables).  Thread 0 streams, per plane of the column, the 8 x 8 tile of W's
-// chunk (one TMA) and the plane's entries -- key = point | slot << 8, sorted
-// by slot, and beta -- (two bulk copies) into a ring of NBUF buffers.  The
-// plane's entries are cut into eight equal runs, one per warp, whatever
-// slot they belong to, so the warps share the work evenly even when one atom
-// fills the column and another only grazes it.  Lane (projector, vector)
-// sums beta * W along its warp's run in registers and flushes the sum into
-// the column's accumulator sAcc[slot][projector][vector] (shared-memory
-// atomics) when the run passes to the next slot; at the end every
-// accumulator goes to Pout with one vector atomic.
+// <b|W> for every atom, by projection columns (an 8 x 8 tile of points, one
+// orbital chunk, PZC planes).  Thread 0 brings the column's W planes (one
+// TMA each) and its entries -- W row (plane * 64 + point) and beta, ordered
+// by (slot, plane, point) -- (two bulk copies) into shared memory, all on
+// one mbarrier.  The entries are cut into eight equal runs, one per warp;
+// a warp walks the atoms (slots) its run overlaps and, for each, the
+// entries in both, with the lanes split over (entry group, projector,
+// 16-byte vector), then adds the atom's sum to Pout with one vector atomic.
+// Every warp does the same work whatever the sizes of the atoms' spheres in
+// the column.
 template <typename R, int VP, int NP>
 __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__ CUtensorMap tm_c, TNl<R> N, int nx,
-                                                         int ny, int nz, int ntx, int zc, int ld, int pcap,
+                                                         int ny, int nz, int ntx, int pzc, int ld, int pcap,
                                                          int* err) {
-    constexpr int NBUF = 4;
     constexpr int OCR = VP * 16 / sizeof(R);
     constexpr int NC = V16<R>::NC;
-    constexpr int PPW = 32 / VP;                    // projectors per warp pass
+    constexpr int PPW = (32 / VP) < NP ? (32 / VP) : NP;    // projectors per warp pass
+    constexpr int EG = 32 / (PPW * VP);                      // entry groups per warp
+    constexpr int NPASS = NP / PPW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    // buffer b: W tile [64][VP] float4, then keys [pcap + 8] int32, then beta [pcap][NP] R;
-    // after the NBUF buffers: sAcc [maxs][NP][VP] float4
-    const uint32_t wbytes = 64 * VP * 16;
-    const uint32_t pbytes = (uint32_t)(pcap + 8) * 4;
-    const uint32_t bbytes = (uint32_t)pcap * NP * sizeof(R);
-    const uint32_t bufbytes = (wbytes + pbytes + bbytes + 127) / 128 * 128;
-    float4* sAcc = reinterpret_cast<float4*>(base + NBUF * bufbytes);
-    __shared__ __align__(8) uint64_t bars[NBUF];
+    // W [pzc][64][VP] float4, rows [pcap + 8] int32, beta [pcap][NP] R
+    const uint32_t wbytes = (uint32_t)pzc * 64 * VP * 16;
+    const uint32_t kbytes = (uint32_t)(pcap + 8) * 4;
+    const float4* sW = reinterpret_cast<const float4*>(base);
+    __shared__ __align__(8) uint64_t bar;
     __shared__ int abort_sh;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int col = blockIdx.x + gridDim.x * blockIdx.z;
+    const int pcol = blockIdx.x + gridDim.x * blockIdx.z;
     const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
-    const int z0 = blockIdx.z * zc;
-    const int nzc = min(zc, nz - z0);
+    const int z0 = blockIdx.z * pzc;
+    const int nzc = min(pzc, nz - z0);
     const int c0 = blockIdx.y * OCR;
-    const int cs = N.col_start[col], na = N.col_start[col + 1] - cs;
-    const int stride = N.maxs + 1;
+    const int k0 = N.pp_atom_start[pcol], k1 = N.pp_atom_start[pcol + 1];   // the column's slots
+    const int e0 = N.pp_seg[k0], e1 = N.pp_seg[k1];
+    if (e1 == e0) return;
+    const int a0 = e0 & ~3, a1 = (e1 + 3) & ~3;
+    const int32_t* sRow = reinterpret_cast<const int32_t*>(base + wbytes) - a0;
+    const R* sB = reinterpret_cast<const R*>(base + wbytes + kbytes) - (int64_t)e0 * NP;
     if (tid == 0) {
-        for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+        mbar_init(&bar, 1);
         abort_sh = 0;
         fence_proxy_async();
+        mbar_expect_tx(&bar, (uint32_t)(a1 - a0) * 4 + (uint32_t)(e1 - e0) * NP * sizeof(R) +
+                                 (uint32_t)nzc * 64 * VP * 16);
+        bulk_g2s(base + wbytes, N.pp_key + a0, (uint32_t)(a1 - a0) * 4, &bar);
+        bulk_g2s(base + wbytes + kbytes, N.pp_beta + (int64_t)e0 * NP, (uint32_t)(e1 - e0) * NP * sizeof(R), &bar);
+        for (int iz = 0; iz < nzc; ++iz) tma_load_4d(base + (size_t)iz * 64 * VP * 16, &tm_c, c0, x0, y0, z0 + iz, &bar);
     }
-    for (int i = tid; i < na * NP * VP; i += 256) sAcc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    if (na == 0) return;
-
-    auto issue = [&](int iz) {      // plane iz of the column into buffer iz % NBUF
-        unsigned char* buf = base + (iz % NBUF) * bufbytes;
-        const int32_t* po = N.pe_off + ((int64_t)col * zc + iz) * stride;
-        const int b0 = po[0], b1 = po[na];
-        const int a0 = b0 & ~3, a1 = (b1 + 3) & ~3;
-        uint32_t bytes = wbytes;
-        if (b1 > b0) bytes += (uint32_t)(a1 - a0) * 4 + (uint32_t)(b1 - b0) * NP * sizeof(R);
-        mbar_expect_tx(&bars[iz % NBUF], bytes);
-        tma_load_4d(buf, &tm_c, c0, x0, y0, z0 + iz, &bars[iz % NBUF]);
-        if (b1 > b0) {
-            bulk_g2s(buf + wbytes, N.pe_point + a0, (uint32_t)(a1 - a0) * 4, &bars[iz % NBUF]);
-            bulk_g2s(buf + wbytes + pbytes, N.pe_beta + (int64_t)b0 * NP, (uint32_t)(b1 - b0) * NP * sizeof(R),
-                     &bars[iz % NBUF]);
-        }
-    };
-    int issued = 0;
-    if (tid == 0) {
-        for (; issued < NBUF && issued < nzc; ++issued) issue(issued);
-    }
-
-    const int jj = lane % VP, pl = lane / VP;
-    auto flush = [&](int s, int pi, const Cv<R>& a) {
-        R* dst = reinterpret_cast<R*>(&sAcc[(s * NP + pi) * VP + jj]);
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    const int T = e1 - e0;
+    const int r0 = e0 + (int)(((int64_t)T * warp) / 8), r1 = e0 + (int)(((int64_t)T * (warp + 1)) / 8);
+    const int eg = lane / (PPW * VP), pl = (lane / VP) % PPW, jj = lane % VP;
+    const int64_t row = 2 * (int64_t)ld;
+    if (ok && r1 > r0) {
+        for (int k = k0; k < k1; ++k) {
+            const int lo = max(r0, N.pp_seg[k]), hi = min(r1, N.pp_seg[k + 1]);
+            if (lo >= hi) continue;
+            const int64_t at = N.pp_atom[k];
 #pragma unroll
-        for (int u = 0; u < NC; ++u) {
-            atomicAdd(dst + 2 * u, a.re[u]);
-            atomicAdd(dst + 2 * u + 1, a.im[u]);
-        }
-    };
-    int waited = 0;
-    for (int iz = 0; iz < nzc; ++iz) {
-        const bool ok = mbar_wait_bounded(&bars[iz % NBUF], (uint32_t)((iz / NBUF) & 1));
-        if (!ok) abort_sh = 1;
-        if (tid == 0) waited = iz + 1;
-        const unsigned char* buf = base + (iz % NBUF) * bufbytes;
-        const float4* sW = reinterpret_cast<const float4*>(buf);
-        const int32_t* po = N.pe_off + ((int64_t)col * zc + iz) * stride;
-        const int b0 = po[0], b1 = po[na], a0 = b0 & ~3;
-        const int32_t* sKey = reinterpret_cast<const int32_t*>(buf + wbytes) - a0;
-        const R* sB = reinterpret_cast<const R*>(buf + wbytes + pbytes) - (int64_t)b0 * NP;
-        // this warp's run of the plane's entries
-        const int T = b1 - b0;
-        const int r0 = b0 + (int)(((int64_t)T * warp) / 8), r1 = b0 + (int)(((int64_t)T * (warp + 1)) / 8);
-        if (ok && r1 > r0) {
+            for (int pass = 0; pass < NPASS; ++pass) {
+                const int pi = pass * PPW + pl;
+                Cv<R> a, b2;
 #pragma unroll
-            for (int pg = 0; pg < (NP + PPW - 1) / PPW; ++pg) {
-                const int pi = pg * PPW + pl;
-                if (pi < NP) {
-                    int cur = sKey[r0] >> 8;
-                    Cv<R> a;
+                for (int u = 0; u < NC; ++u) { a.re[u] = 0; a.im[u] = 0; b2.re[u] = 0; b2.im[u] = 0; }
+                int e = lo + eg;
+                for (; e + EG < hi; e += 2 * EG) {          // two independent entries in flight
+                    const R bv0 = sB[(int64_t)e * NP + pi], bv1 = sB[(int64_t)(e + EG) * NP + pi];
+                    Cv<R> w0, w1;
+                    unpack(sW[sRow[e] * VP + jj], w0);
+                    unpack(sW[sRow[e + EG] * VP + jj], w1);
 #pragma unroll
-                    for (int u = 0; u < NC; ++u) { a.re[u] = 0; a.im[u] = 0; }
-                    for (int e = r0; e < r1; ++e) {
-                        const int key = sKey[e], s = key >> 8;
-                        if (s != cur) {
-                            flush(cur, pi, a);
-#pragma unroll
-                            for (int u = 0; u < NC; ++u) { a.re[u] = 0; a.im[u] = 0; }
-                            cur = s;
-                        }
-                        const R bv = sB[(int64_t)e * NP + pi];
-                        Cv<R> w;
-                        unpack(sW[(key & 63) * VP + jj], w);
-#pragma unroll
-                        for (int u = 0; u < NC; ++u) { a.re[u] += bv * w.re[u]; a.im[u] += bv * w.im[u]; }
+                    for (int u = 0; u < NC; ++u) {
+                        a.re[u] += bv0 * w0.re[u]; a.im[u] += bv0 * w0.im[u];
+                        b2.re[u] += bv1 * w1.re[u]; b2.im[u] += bv1 * w1.im[u];
                     }
-                    flush(cur, pi, a);
                 }
+                if (e < hi) {
+                    const R bv0 = sB[(int64_t)e * NP + pi];
+                    Cv<R> w0;
+                    unpack(sW[sRow[e] * VP + jj], w0);
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) { a.re[u] += bv0 * w0.re[u]; a.im[u] += bv0 * w0.im[u]; }
+                }
+#pragma unroll
+                for (int u = 0; u < NC; ++u) { a.re[u] += b2.re[u]; a.im[u] += b2.im[u]; }
+                global_add(N.Pout + (at * NP + pi) * row + c0 + jj * (16 / (int)sizeof(R)), pack(a), N.dV);
             }
         }
-        __syncthreads();                    // buffer iz % NBUF is free again
-        if (abort_sh) break;
-        if (tid == 0 && issued < nzc) {
-            fence_proxy_async();
-            issue(issued);
-            ++issued;
-        }
     }
-    if (abort_sh) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            for (int iz = waited; iz < issued; ++iz) (void)mbar_wait_bounded(&bars[iz % NBUF], (uint32_t)((iz / NBUF) & 1));
-        }
-        return;
-    }
+    if (!ok) abort_sh = 1;
     __syncthreads();
-    const int64_t row = 2 * (int64_t)ld;
-    for (int i = tid; i < na * NP * VP; i += 256) {
-        const int s = i / (NP * VP), r = i - s * (NP * VP), pi = r / VP, j = r - pi * VP;
-        const int64_t a = N.col_atom[cs + s];
-        global_add(N.Pout + (a * NP + pi) * row + c0 + j * (16 / (int)sizeof(R)), sAcc[i], N.dV);
+    if (tid == 0 && abort_sh) {
+        atomicExch(err, 1);
+        (void)mbar_wait_bounded(&bar, 0);     // copies still in flight land before the CTA exits
     }
 }
 
 template <typename R, int VP>
-size_t project_smem(int np, int pcap, int maxs) {
-    const size_t w = 64 * VP * 16, p = (size_t)(pcap + 8) * 4, b = (size_t)pcap * np * sizeof(R);
-    return 4 * ((w + p + b + 127) / 128 * 128) + (size_t)maxs * np * VP * 16 + 128;
+size_t project_smem(int np, int pcap, int pzc) {
+    return (size_t)pzc * 64 * VP * 16 + (size_t)(pcap + 8) * 4 + (size_t)pcap * np * sizeof(R) + 128;
 }
 
 // ---------------------------------------------------------------------------
@@ -679,9 +642,11 @@ void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool
         N.D = static_cast<const R*>(t.D);
         N.Pin = static_cast<const R*>(a.P);
         N.Pout = proj ? static_cast<R*>(a.P_out) : nullptr;
-        N.pe_off = t.pe_off;
-        N.pe_point = t.pe_point;
-        N.pe_beta = static_cast<const R*>(t.pe_beta);
+        N.pp_seg = t.pp_seg;
+        N.pp_atom_start = t.pp_atom_start;
+        N.pp_atom = t.pp_atom;
+        N.pp_key = t.pp_key;
+        N.pp_beta = static_cast<const R*>(t.pp_beta);
         N.dV = (R)(d.desc.h * d.desc.h * d.desc.h);
         N.maxs = t.maxs;
     }
@@ -702,11 +667,12 @@ void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool
         if (!proj) return;
         N.Pout = static_cast<R*>(a.P_out);
         const TmaMaps mo = maps_for(d, a.out);
-        const size_t psm = project_smem<R, VP>(NP, t.pcap, t.maxs);
+        const size_t psm = project_smem<R, VP>(NP, t.pcap, t.pzc);
+        const dim3 pgrid(grid.x, grid.y, (G.nz + t.pzc - 1) / t.pzc);
         auto pk = k_nl_project_cols<R, VP, NP>;
         ensure_dynamic_smem(reinterpret_cast<const void*>(pk), psm);
         ProfScope ps(d.prof, MLMD_KERNEL_PROJECT, d.stream);
-        pk<<<grid, 256, psm, d.stream>>>(mo.centre, N, G.nx, G.ny, G.nz, G.ntx, G.zc, G.ld, t.pcap, d.err_flag);
+        pk<<<pgrid, 256, psm, d.stream>>>(mo.centre, N, G.nx, G.ny, G.nz, G.ntx, t.pzc, G.ld, t.pcap, d.err_flag);
         d.launches++;
     }
 }
@@ -797,11 +763,11 @@ void tma_release(Domain& d) {
 void tma_build_nl(Domain& d, const double* D_host) {
     if (!d.tma || !d.tma->ok) return;
     TmaState& t = *d.tma;
-    for (void* p : {(void*)t.col_start, (void*)t.col_atom, (void*)t.ent_slot, t.ent_beta, t.D, (void*)t.pe_off,
-                    (void*)t.pe_point, t.pe_beta})
+    for (void* p : {(void*)t.col_start, (void*)t.col_atom, (void*)t.ent_slot, t.ent_beta, t.D, (void*)t.pp_seg,
+                    (void*)t.pp_atom_start, (void*)t.pp_atom, (void*)t.pp_key, t.pp_beta})
         if (p) d.mem.put(p);
-    t.col_start = t.col_atom = t.ent_slot = t.pe_off = t.pe_point = nullptr;
-    t.ent_beta = t.D = t.pe_beta = nullptr;
+    t.col_start = t.col_atom = t.ent_slot = t.pp_seg = t.pp_atom_start = t.pp_atom = t.pp_key = nullptr;
+    t.ent_beta = t.D = t.pp_beta = nullptr;
     t.nl_ok = false;
     t.maxs = 0;
     const Nonlocal& nl = d.nl;
@@ -859,47 +825,67 @@ void tma_build_nl(Domain& d, const double* D_host) {
         if (rs == 4) reinterpret_cast<float*>(Dr.data())[k] = (float)D_host[k];
         else reinterpret_cast<double*>(Dr.data())[k] = D_host[k];
     }
-    // per (column, plane, slot) lists of (point, beta) for the output projection
-    const int M = std::max(t.maxs, 1);
-    const int64_t ngrp = (int64_t)t.ncols * t.zc;
-    std::vector<int32_t> pcnt((size_t)ngrp * M + 1, 0);
-    auto key_of = [&](int64_t g, int slot) {
-        const int z = (int)(g / ((int64_t)nx * ny));
-        return ((int64_t)col_of(g) * t.zc + (z % t.zc)) * M + slot;
+    // projection tables: projection columns of pzc planes, entries ordered by
+    // (slot, plane, point); slots number a column's atoms in ascending order
+    t.pzc = std::min(4, t.zc);
+    const int nzp = (d.desc.n[2] + t.pzc - 1) / t.pzc;
+    const int64_t ncp = (int64_t)ntiles * nzp;
+    auto pcol_of = [&](int64_t g) {
+        const int x = (int)(g % nx), y = (int)((g / nx) % ny), z = (int)(g / ((int64_t)nx * ny));
+        return (int64_t)(x / TX + ntx * (y / TY)) + ntiles * (z / t.pzc);
     };
-    for (int64_t q = 0; q < nl.n_list; ++q) pcnt[key_of(idx[q], qslot[q])]++;
-    std::vector<int32_t> pst((size_t)ngrp * M + 1, 0);
-    for (size_t k = 0; k + 1 < pst.size(); ++k) pst[k + 1] = pst[k] + pcnt[k];
-    std::vector<int32_t> pe_off((size_t)ngrp * (M + 1));
-    for (int64_t gr = 0; gr < ngrp; ++gr)
-        for (int s2 = 0; s2 <= M; ++s2) pe_off[gr * (M + 1) + s2] = pst[gr * M + s2];
-    std::vector<int32_t> pe_point(nl.n_list), pcur((size_t)ngrp * M, 0);
-    std::vector<unsigned char> pe_beta((size_t)nl.n_list * np * rs);
+    std::vector<std::vector<int32_t>> patoms(ncp);
+    std::vector<int32_t> plast(ncp, -1), pslot(nl.n_list);
+    for (int a = 0; a < nl.n_atoms; ++a)
+        for (int64_t q = nl.h_off[a]; q < nl.h_off[a + 1]; ++q) {
+            const int64_t c = pcol_of(idx[q]);
+            if (plast[c] != a) { patoms[c].push_back(a); plast[c] = a; }
+            pslot[q] = (int32_t)patoms[c].size() - 1;
+        }
+    // atoms are visited in ascending order and each atom's points in ascending
+    // grid order, so counting by (column, slot, plane) gives the wanted order
+    std::vector<int32_t> pp_atom_start(ncp + 1, 0), pp_atom;
+    for (int64_t c = 0; c < ncp; ++c) {
+        pp_atom_start[c + 1] = pp_atom_start[c] + (int32_t)patoms[c].size();
+        pp_atom.insert(pp_atom.end(), patoms[c].begin(), patoms[c].end());
+    }
+    auto pkey_of = [&](int64_t q) {     // (column, slot, plane) bucket
+        const int64_t g = idx[q];
+        const int z = (int)(g / ((int64_t)nx * ny));
+        return ((int64_t)pp_atom_start[pcol_of(g)] + pslot[q]) * t.pzc + (z % t.pzc);
+    };
+    const int64_t nbk = (int64_t)pp_atom_start[ncp] * t.pzc;
+    std::vector<int32_t> bcnt(nbk + 1, 0);
+    for (int64_t q = 0; q < nl.n_list; ++q) bcnt[pkey_of(q) + 1]++;
+    for (int64_t k = 0; k < nbk; ++k) bcnt[k + 1] += bcnt[k];
+    const int64_t nslots = pp_atom_start[ncp];
+    std::vector<int32_t> pp_seg(nslots + 1, 0);
+    for (int64_t k = 0; k <= nslots; ++k) pp_seg[k] = bcnt[k * t.pzc];
+    std::vector<int32_t> pp_key(nl.n_list + 8, 0);
+    std::vector<unsigned char> pp_beta((size_t)nl.n_list * np * rs);
     for (int a = 0; a < nl.n_atoms; ++a)
         for (int64_t q = nl.h_off[a]; q < nl.h_off[a + 1]; ++q) {
             const int64_t g = idx[q];
-            const int64_t k = key_of(g, qslot[q]);
-            const int64_t e = pst[k] + pcur[k]++;
-            pe_point[e] = (int32_t)((((g / nx) % ny) % TY) * TX + (g % nx) % TX) | (qslot[q] << 8);
+            const int64_t e = bcnt[pkey_of(q)]++;
+            const int z = (int)(g / ((int64_t)nx * ny));
+            pp_key[e] = (int32_t)((((g / nx) % ny) % TY) * TX + (g % nx) % TX) + (z % t.pzc) * 64;
             for (int i = 0; i < np; ++i) {
-                if (rs == 4) reinterpret_cast<float*>(pe_beta.data())[e * np + i] = (float)beta[q * np + i];
-                else reinterpret_cast<double*>(pe_beta.data())[e * np + i] = beta[q * np + i];
+                if (rs == 4) reinterpret_cast<float*>(pp_beta.data())[e * np + i] = (float)beta[q * np + i];
+                else reinterpret_cast<double*>(pp_beta.data())[e * np + i] = beta[q * np + i];
             }
         }
-    // most entries of one (column, plane): the projection kernel's buffers
     int pcap = 0;
-    for (int64_t gr = 0; gr < ngrp; ++gr) pcap = std::max(pcap, pe_off[gr * (M + 1) + M] - pe_off[gr * (M + 1)]);
+    for (int64_t c = 0; c < ncp; ++c) pcap = std::max(pcap, pp_seg[pp_atom_start[c + 1]] - pp_seg[pp_atom_start[c]]);
     t.pcap = (pcap + 3) / 4 * 4;
-    pe_point.resize(pe_point.size() + 8, 0);        // slack for copies rounded out to 16 bytes
     size_t sm8 = 0, sm4 = 0;
     if (d.c64()) {
         sm8 = std::max(np == 4 ? smem_bytes<float, 8, 4>(t.maxs) : smem_bytes<float, 8, 8>(t.maxs),
-                       project_smem<float, 8>(np, t.pcap, t.maxs));
+                       project_smem<float, 8>(np, t.pcap, t.pzc));
         sm4 = std::max(np == 4 ? smem_bytes<float, 4, 4>(t.maxs) : smem_bytes<float, 4, 8>(t.maxs),
-                       project_smem<float, 4>(np, t.pcap, t.maxs));
+                       project_smem<float, 4>(np, t.pcap, t.pzc));
     } else {
         sm8 = sm4 = std::max(np == 4 ? smem_bytes<double, 8, 4>(t.maxs) : smem_bytes<double, 8, 8>(t.maxs),
-                             project_smem<double, 8>(np, t.pcap, t.maxs));
+                             project_smem<double, 8>(np, t.pcap, t.pzc));
     }
     const size_t kMaxSmem = 200 * 1024;
     if (sm4 > kMaxSmem) return;   // too many atoms per column for the staging: plain kernel
@@ -920,12 +906,16 @@ void tma_build_nl(Domain& d, const double* D_host) {
     MLMD_CUDA(cudaMemcpyAsync(t.ent_slot, ent_slot.data(), sizeof(int32_t) * ent_slot.size(), cudaMemcpyHostToDevice, d.stream));
     MLMD_CUDA(cudaMemcpyAsync(t.ent_beta, ent_beta.data(), ent_beta.size(), cudaMemcpyHostToDevice, d.stream));
     MLMD_CUDA(cudaMemcpyAsync(t.D, Dr.data(), Dr.size(), cudaMemcpyHostToDevice, d.stream));
-    t.pe_off = (int32_t*)d.mem.get(sizeof(int32_t) * pe_off.size());
-    t.pe_point = (int32_t*)d.mem.get(sizeof(int32_t) * pe_point.size());
-    t.pe_beta = d.mem.get(pe_beta.size());
-    MLMD_CUDA(cudaMemcpyAsync(t.pe_off, pe_off.data(), sizeof(int32_t) * pe_off.size(), cudaMemcpyHostToDevice, d.stream));
-    MLMD_CUDA(cudaMemcpyAsync(t.pe_point, pe_point.data(), sizeof(int32_t) * pe_point.size(), cudaMemcpyHostToDevice, d.stream));
-    MLMD_CUDA(cudaMemcpyAsync(t.pe_beta, pe_beta.data(), pe_beta.size(), cudaMemcpyHostToDevice, d.stream));
+    auto upload = [&](const void* src, size_t bytes) {
+        void* p = d.mem.get(std::max<size_t>(bytes, 16));
+        if (bytes) MLMD_CUDA(cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, d.stream));
+        return p;
+    };
+    t.pp_seg = (int32_t*)upload(pp_seg.data(), sizeof(int32_t) * pp_seg.size());
+    t.pp_atom_start = (int32_t*)upload(pp_atom_start.data(), sizeof(int32_t) * pp_atom_start.size());
+    t.pp_atom = (int32_t*)upload(pp_atom.data(), sizeof(int32_t) * pp_atom.size());
+    t.pp_key = (int32_t*)upload(pp_key.data(), sizeof(int32_t) * pp_key.size());
+    t.pp_beta = upload(pp_beta.data(), pp_beta.size());
     MLMD_CUDA(cudaStreamSynchronize(d.stream));
     t.nl_ok = true;
 }
