@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "mlmd_internal.cuh"
 
@@ -140,7 +141,8 @@ template <typename R> struct TGeo {
     int zc;        // planes per CTA
 };
 
-// Shared-memory slot: centre [TY][TX][VP], xm/xp [TY][2][VP], ym/yp [2][TX][VP] (16-byte vectors)
+// Shared-memory slot of w: centre [TY][TX][VP], xm/xp [TY][2][VP], ym/yp
+// [2][TX][VP] (16-byte vectors).  psi's centre tiles have a ring of their own.
 template <int VP> struct Slot {
     static constexpr int C = 0;
     static constexpr int XM = C + TY * TX * VP;
@@ -149,7 +151,10 @@ template <int VP> struct Slot {
     static constexpr int YP = YM + 2 * TX * VP;
     static constexpr int N = YP + 2 * TX * VP;    // vectors per slot
     static constexpr uint32_t BYTES = N * 16;
+    static constexpr int PN = TY * TX * VP;       // vectors of a psi tile
+    static constexpr uint32_t PSI_BYTES = PN * 16;
 };
+constexpr int PSL = 3;                            // psi ring slots
 
 // Vector (x+dx, y+dy) of the plane in slot s, one of dx, dy zero, |d| <= 2.
 template <int VP>
@@ -159,6 +164,16 @@ __device__ __forceinline__ const float4* nb_ptr(const float4* s, int x, int y, i
     if (y < 0) return s + Slot<VP>::YM + ((y + 2) * TX + x) * VP + j;
     if (y >= TY) return s + Slot<VP>::YP + ((y - TY) * TX + x) * VP + j;
     return s + Slot<VP>::C + (y * TX + x) * VP + j;
+}
+
+// With 128-byte chunks (VP = 8) the tiles arrive with TMA's 128-byte swizzle:
+// the 16-byte vector v of a 128-byte row at float4 offset o (a multiple of 8,
+// measured from a 1024-byte aligned base) sits at o + (v ^ (o / 8 mod 8)).
+// That spreads the same vector of eight consecutive points over all banks.
+template <int VP>
+__device__ __forceinline__ int swz(int o, int v) {
+    if constexpr (VP == 8) return o + (v ^ ((o >> 3) & 7));
+    else return o + v;
 }
 
 
@@ -204,10 +219,21 @@ __device__ __forceinline__ void global_add(double* p, float4 v, double s) {
     atomicAdd(p + 1, s * d.y);
 }
 
-template <typename R, int ORDER, int VP, int NP, int NSLOT, int TPP>
+// packed pairs of FP32 (Blackwell f32x2 arithmetic): one complex64 value
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(make_float2(-1.f, -1.f), b, a); }
+__device__ __forceinline__ float2 f2s(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 swp(float2 v) { return make_float2(v.y, v.x); }
+
+template <typename R, int ORDER, int VP, int NP, int NSLOT, int TPP, bool OBS>
 __global__ void __launch_bounds__(64 * TPP, 2)
     k_stage_tma(const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_x,
-                const __grid_constant__ CUtensorMap tm_y, TGeo<R> G, const R* psi, R* out,
+                const __grid_constant__ CUtensorMap tm_y, const __grid_constant__ CUtensorMap tm_p, int psi_mode,
+                TGeo<R> G, R* out,
                 const R* __restrict__ V, const R* __restrict__ f, const double* __restrict__ Ak, TNl<R> N,
                 R gre, R gim, double* __restrict__ obs, int* err) {
     constexpr int NC = V16<R>::NC;
@@ -217,29 +243,42 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     constexpr int NPV = (NP > 0 ? NP : 1);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations on a 128-byte boundary (the launch adds 128 bytes of slack)
-    float4* ring = reinterpret_cast<float4*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-    float4* sP = ring + NSLOT * Slot<VP>::N;        // [maxs][NP][VP] staged <b|w>
+    // TMA destinations on a 1024-byte boundary (the launch adds 1024 bytes of
+    // slack): the swizzle pattern is a function of the address bits
+    float4* ring = reinterpret_cast<float4*>(smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u));
+    float4* sPsi = ring + NSLOT * Slot<VP>::N;      // [PSL][TY][TX][VP] psi tiles
+    float4* sP = sPsi + PSL * Slot<VP>::PN;         // [maxs][NP][VP] staged <b|w>
     R* sD = reinterpret_cast<R*>(sP + N.maxs * NPV * VP);   // [maxs][NP]
     __shared__ __align__(8) uint64_t bars[NSLOT];
+    __shared__ __align__(8) uint64_t pbars[PSL];
     __shared__ R sA[4];
     __shared__ int abort_sh;
 
     const int tid = threadIdx.x;
     const int pt = tid / TPP, jv = tid % TPP;       // point of the tile, first vector (then jv + TPP k)
     const int lx = pt % TX, ly = pt / TX;
-    const int tile = blockIdx.x;
+    // grid (chunk, tile, z range): the chunks of one tile run side by side,
+    // so each grid point's orbital row is read from DRAM in one stretch
+    const int tile = blockIdx.y;
     const int x0 = (tile % G.ntx) * TX, y0 = (tile / G.ntx) * TY;
-    const int chunk = blockIdx.y;
+    const int chunk = blockIdx.x;
     const int z0 = blockIdx.z * G.zc;
     const int nzc = min(G.zc, G.nz - z0);           // planes computed by this CTA
     const int nplanes = nzc + 4;                    // planes z0-2 .. z0+nzc+1
     const int c0 = chunk * OCR;                     // first real of the chunk within a row
-    const bool has_psi = psi != nullptr;
-    const bool do_obs = obs != nullptr;
-    const int col = blockIdx.x + gridDim.x * blockIdx.z;
+    // psi_mode 0: out = gamma h w; 1: psi is w itself (its centre tile is in
+    // the ring already); 2: psi's centre tile comes with each plane
+    const bool has_psi = psi_mode != 0;
+    // complex64 launches without observables take the packed path: h w as
+    // sum_n c_n w_n with the complex coefficient c_n = k_n - i a_n of each
+    // stencil neighbour (k from the Laplacian, a = A . gradient weight),
+    // evaluated as f32x2 multiply-adds on (re, im) pairs
+    constexpr bool FAST = std::is_same<R, float>::value && !OBS;
+    const int col = tile + gridDim.y * blockIdx.z;
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < PSL; ++s) mbar_init(&pbars[s], 1);
         abort_sh = 0;
         fence_proxy_async();
     }
@@ -274,24 +313,40 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         tma_load_4d(d + Slot<VP>::YP, &tm_y, c0, x0, (y0 + TY) % G.ny, zz, b);
     };
     auto wait_plane = [&](int p) -> bool { return mbar_wait_bounded(&bars[p % NSLOT], (uint32_t)((p / NSLOT) & 1)); };
+    // psi tile of computed plane j (z = z0 + j) into psi slot j % PSL
+    int issued_p = 0, waited_p = 0;                 // meaningful in thread 0
+    auto issue_psi = [&](int j) {
+        if (psi_mode != 2 || j >= nzc) return;
+        uint64_t* b = &pbars[j % PSL];
+        mbar_expect_tx(b, Slot<VP>::PSI_BYTES);
+        tma_load_4d(sPsi + (j % PSL) * Slot<VP>::PN, &tm_p, c0, x0, y0, z0 + j, b);
+        issued_p = j + 1;
+    };
 
     // shared-memory offsets (16-byte vectors) of this thread's first vector and
     // of its x-y neighbours within a slot; vector k adds 4 k
-    const int offC = Slot<VP>::C + (ly * TX + lx) * VP + jv;
+    // this thread's vectors of its point: vb + k, k < NVT (NVT is 1 or 2, vb
+    // even when NVT = 2, so the vector k of a row sits at the row's vector-0
+    // address XOR k)
+    static_assert(NVT == 1 || NVT == 2, "one or two vectors per thread");
+    const int vb = jv * NVT;
+    const int offC = swz<VP>(Slot<VP>::C + (ly * TX + lx) * VP, vb);
+    const int offPs = swz<VP>(pt * VP, vb);        // within a psi tile
     int offN[8];
     {
         const int dx[8] = {1, -1, 0, 0, 2, -2, 0, 0}, dy[8] = {0, 0, 1, -1, 0, 0, 2, -2};
 #pragma unroll
-        for (int n = 0; n < 8; ++n) offN[n] = (int)(nb_ptr<VP>(ring, lx + dx[n], ly + dy[n], jv) - ring);
+        for (int n = 0; n < 8; ++n) offN[n] = swz<VP>((int)(nb_ptr<VP>(ring, lx + dx[n], ly + dy[n], 0) - ring), vb);
     }
 
     int issued = 0, waited = 0;                     // meaningful in thread 0
     if (tid == 0) {
         for (int p = 0; p < NSLOT && p < nplanes; ++p) issue(p);
         issued = min(NSLOT, nplanes);
+        for (int j = 0; j < PSL - 1; ++j) issue_psi(j);
     }
     // register window of the thread's vectors: q[k][0..4] = planes z-2 .. z+2
-    Cv<R> q[NVT][5];
+    float4 q[NVT][5];
     bool ok = true;
     for (int p = 0; p < 4; ++p) ok = ok && wait_plane(p);
     if (!ok) abort_sh = 1;
@@ -301,7 +356,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         for (int p = 0; p < 4; ++p) {
             const float4* s = ring + (p % NSLOT) * Slot<VP>::N;
 #pragma unroll
-            for (int k = 0; k < NVT; ++k) unpack(s[offC + TPP * k], q[k][p]);
+            for (int k = 0; k < NVT; ++k) q[k][p] = s[offC ^ k];
         }
     }
     if (tid == 0) waited = aborted0 ? 0 : 4;
@@ -319,14 +374,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     // nonlocal entry range of this thread's point, one plane ahead
     int e0n = 0, e1n = 0;
     if (NP > 0 && nzc > 0) { e0n = N.pstart[g]; e1n = N.pstart[g + 1]; }
+    R vnext = nzc > 0 ? V[g] : (R)0;       // V one plane ahead
     for (int i = 0; i < nzc && !aborted0; ++i, g += plane_stride) {
         // per-point global loads first, so that they overlap the plane wait
         // and the shared-memory stencil
-        const R vv = V[g];
-        float4 pp[NVT];
-        if (has_psi)
-#pragma unroll
-            for (int k = 0; k < NVT; ++k) pp[k] = *(reinterpret_cast<const float4*>(psi + g * row + c0) + jv + TPP * k);
+        const R vv = vnext;
+        if (i + 1 < nzc) vnext = V[g + plane_stride];
         const int e0 = e0n, e1 = e1n;
         int sf = 0;
         R bf[NPV];
@@ -344,65 +397,118 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         if (abort_sh) break;
         if (tid == 0) {
             waited = i + 5;
+            fence_proxy_async();
             if (issued < nplanes) {         // next plane into the slot of plane z-1
-                fence_proxy_async();
                 issue(issued);
                 ++issued;
             }
+            issue_psi(i + PSL - 1);         // into the psi slot of plane z-1
         }
         const float4* sc = ring + ((i + 2) % NSLOT) * Slot<VP>::N;    // plane z
         const float4* s4 = ring + ((i + 4) % NSLOT) * Slot<VP>::N;    // plane z+2
-        Cv<R> hw[NVT], dd[NVT][3];
+        Cv<R> hw[NVT], dd[NVT][OBS ? 3 : 1];
+        float2 hp[NVT][2];                  // packed path: h w of the vector's two complex values
+        if constexpr (FAST) {
+            const float2 kk1 = f2s((float)G.kc1), kk2 = f2s((float)G.kc2);
+            const float2 cd = f2s((float)(G.kc0 + sA[3] + vv));
+            float2 a1[3], a2[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) { a1[ax] = f2s((float)(sA[ax] * G.gk1)); a2[ax] = f2s((float)(sA[ax] * G.gk2)); }
+#pragma unroll
+            for (int k = 0; k < NVT; ++k) {
+                q[k][4] = s4[offC ^ k];
+                float4 p1[3], m1[3], p2[3], m2[3];
+#pragma unroll
+                for (int ax = 0; ax < 2; ++ax) {
+                    p1[ax] = sc[(offN[2 * ax]) ^ k];
+                    m1[ax] = sc[(offN[2 * ax + 1]) ^ k];
+                    if (ORDER == 4) {
+                        p2[ax] = sc[(offN[4 + 2 * ax]) ^ k];
+                        m2[ax] = sc[(offN[5 + 2 * ax]) ^ k];
+                    }
+                }
+                p1[2] = q[k][3]; m1[2] = q[k][1]; p2[2] = q[k][4]; m2[2] = q[k][0];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    auto part = [&](float4 v) { return h == 0 ? lo2(v) : hi2(v); };
+                    float2 s1 = f2add(f2add(part(p1[0]), part(m1[0])), f2add(part(p1[1]), part(m1[1])));
+                    s1 = f2add(s1, f2add(part(p1[2]), part(m1[2])));
+                    float2 hk = f2mul(kk1, s1);
+                    float2 ha = f2mul(a1[0], f2sub(part(p1[0]), part(m1[0])));
+                    ha = f2fma(a1[1], f2sub(part(p1[1]), part(m1[1])), ha);
+                    ha = f2fma(a1[2], f2sub(part(p1[2]), part(m1[2])), ha);
+                    if (ORDER == 4) {
+                        float2 s2 = f2add(f2add(part(p2[0]), part(m2[0])), f2add(part(p2[1]), part(m2[1])));
+                        s2 = f2add(s2, f2add(part(p2[2]), part(m2[2])));
+                        hk = f2fma(kk2, s2, hk);
+#pragma unroll
+                        for (int ax = 0; ax < 3; ++ax) ha = f2fma(a2[ax], f2sub(part(p2[ax]), part(m2[ax])), ha);
+                    }
+                    hk = f2fma(cd, part(q[k][2]), hk);
+                    // h w = hk - i ha
+                    hp[k][h] = f2fma(make_float2(1.f, -1.f), swp(ha), hk);
+                }
+            }
+        } else {
 #pragma unroll
         for (int k = 0; k < NVT; ++k) {
-            unpack(s4[offC + TPP * k], q[k][4]);
-            const Cv<R>& c = q[k][2];
+            q[k][4] = s4[offC ^ k];
+            Cv<R> qq[5];
+#pragma unroll
+            for (int w = 0; w < 5; ++w) unpack(q[k][w], qq[w]);
+            const Cv<R>& c = qq[2];
             Cv<R> lap, t1, t2, t3, t4;
+            Cv<R> dl[3];
 #pragma unroll
             for (int e = 0; e < NC; ++e) { lap.re[e] = G.kc0 * c.re[e]; lap.im[e] = G.kc0 * c.im[e]; }
 #pragma unroll
             for (int ax = 0; ax < 2; ++ax) {
-                unpack(sc[offN[2 * ax] + TPP * k], t1);
-                unpack(sc[offN[2 * ax + 1] + TPP * k], t2);
+                unpack(sc[(offN[2 * ax]) ^ k], t1);
+                unpack(sc[(offN[2 * ax + 1]) ^ k], t2);
                 if (ORDER == 4) {
-                    unpack(sc[offN[4 + 2 * ax] + TPP * k], t3);
-                    unpack(sc[offN[5 + 2 * ax] + TPP * k], t4);
+                    unpack(sc[(offN[4 + 2 * ax]) ^ k], t3);
+                    unpack(sc[(offN[5 + 2 * ax]) ^ k], t4);
                 }
 #pragma unroll
                 for (int e = 0; e < NC; ++e) {
                     lap.re[e] += G.kc1 * (t1.re[e] + t2.re[e]);
                     lap.im[e] += G.kc1 * (t1.im[e] + t2.im[e]);
-                    dd[k][ax].re[e] = G.gk1 * (t1.re[e] - t2.re[e]);
-                    dd[k][ax].im[e] = G.gk1 * (t1.im[e] - t2.im[e]);
+                    dl[ax].re[e] = G.gk1 * (t1.re[e] - t2.re[e]);
+                    dl[ax].im[e] = G.gk1 * (t1.im[e] - t2.im[e]);
                     if (ORDER == 4) {
                         lap.re[e] += G.kc2 * (t3.re[e] + t4.re[e]);
                         lap.im[e] += G.kc2 * (t3.im[e] + t4.im[e]);
-                        dd[k][ax].re[e] += G.gk2 * (t3.re[e] - t4.re[e]);
-                        dd[k][ax].im[e] += G.gk2 * (t3.im[e] - t4.im[e]);
+                        dl[ax].re[e] += G.gk2 * (t3.re[e] - t4.re[e]);
+                        dl[ax].im[e] += G.gk2 * (t3.im[e] - t4.im[e]);
                     }
                 }
             }
 #pragma unroll
             for (int e = 0; e < NC; ++e) {
-                lap.re[e] += G.kc1 * (q[k][3].re[e] + q[k][1].re[e]);
-                lap.im[e] += G.kc1 * (q[k][3].im[e] + q[k][1].im[e]);
-                dd[k][2].re[e] = G.gk1 * (q[k][3].re[e] - q[k][1].re[e]);
-                dd[k][2].im[e] = G.gk1 * (q[k][3].im[e] - q[k][1].im[e]);
+                lap.re[e] += G.kc1 * (qq[3].re[e] + qq[1].re[e]);
+                lap.im[e] += G.kc1 * (qq[3].im[e] + qq[1].im[e]);
+                dl[2].re[e] = G.gk1 * (qq[3].re[e] - qq[1].re[e]);
+                dl[2].im[e] = G.gk1 * (qq[3].im[e] - qq[1].im[e]);
                 if (ORDER == 4) {
-                    lap.re[e] += G.kc2 * (q[k][4].re[e] + q[k][0].re[e]);
-                    lap.im[e] += G.kc2 * (q[k][4].im[e] + q[k][0].im[e]);
-                    dd[k][2].re[e] += G.gk2 * (q[k][4].re[e] - q[k][0].re[e]);
-                    dd[k][2].im[e] += G.gk2 * (q[k][4].im[e] - q[k][0].im[e]);
+                    lap.re[e] += G.kc2 * (qq[4].re[e] + qq[0].re[e]);
+                    lap.im[e] += G.kc2 * (qq[4].im[e] + qq[0].im[e]);
+                    dl[2].re[e] += G.gk2 * (qq[4].re[e] - qq[0].re[e]);
+                    dl[2].im[e] += G.gk2 * (qq[4].im[e] - qq[0].im[e]);
                 }
             }
             const R diag = vv + sA[3];
 #pragma unroll
             for (int e = 0; e < NC; ++e) {
-                const R gr = sA[0] * dd[k][0].re[e] + sA[1] * dd[k][1].re[e] + sA[2] * dd[k][2].re[e];
-                const R gi = sA[0] * dd[k][0].im[e] + sA[1] * dd[k][1].im[e] + sA[2] * dd[k][2].im[e];
+                const R gr = sA[0] * dl[0].re[e] + sA[1] * dl[1].re[e] + sA[2] * dl[2].re[e];
+                const R gi = sA[0] * dl[0].im[e] + sA[1] * dl[1].im[e] + sA[2] * dl[2].im[e];
                 hw[k].re[e] = lap.re[e] + diag * c.re[e] + gi;
                 hw[k].im[e] = lap.im[e] + diag * c.im[e] - gr;
             }
+            if constexpr (OBS) {
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) dd[k][ax] = dl[ax];
+            }
+        }
         }
         if (NP > 0) {           // scatter-back: sum_(a,i) b_ai(r) D_ai <b_ai|w>
             for (int e = e0; e < e1; ++e) {
@@ -420,23 +526,47 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                     const R bd = b[pi];
 #pragma unroll
                     for (int k = 0; k < NVT; ++k) {
-                        Cv<R> pv;
-                        unpack(sP[(s * NPV + pi) * VP + jv + TPP * k], pv);
+                        const float4 pv4 = sP[(s * NPV + pi) * VP + vb + k];
+                        if constexpr (FAST) {
+                            hp[k][0] = f2fma(f2s((float)bd), lo2(pv4), hp[k][0]);
+                            hp[k][1] = f2fma(f2s((float)bd), hi2(pv4), hp[k][1]);
+                        } else {
+                            Cv<R> pv;
+                            unpack(pv4, pv);
 #pragma unroll
-                        for (int u = 0; u < NC; ++u) {
-                            hw[k].re[u] += bd * pv.re[u];
-                            hw[k].im[u] += bd * pv.im[u];
+                            for (int u = 0; u < NC; ++u) {
+                                hw[k].re[u] += bd * pv.re[u];
+                                hw[k].im[u] += bd * pv.im[u];
+                            }
                         }
                     }
                 }
             }
         }
+        if (psi_mode == 2) {                // psi tile of this plane (issued two planes ago)
+            if (!mbar_wait_bounded(&pbars[i % PSL], (uint32_t)((i / PSL) & 1))) abort_sh = 1;
+            if (tid == 0) waited_p = i + 1;
+        }
 #pragma unroll
         for (int k = 0; k < NVT; ++k) {
+            if constexpr (FAST) {
+                const float4 ps = psi_mode == 1 ? q[k][2]
+                                  : psi_mode == 2 ? sPsi[(i % PSL) * Slot<VP>::PN + (offPs ^ k)]
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                // out = psi + gamma h w, gamma = gre + i gim
+                const float2 gr2 = f2s((float)gre), gi2 = make_float2(-(float)gim, (float)gim);
+                const float2 o0 = f2fma(gi2, swp(hp[k][0]), f2fma(gr2, hp[k][0], lo2(ps)));
+                const float2 o1 = f2fma(gi2, swp(hp[k][1]), f2fma(gr2, hp[k][1], hi2(ps)));
+                *(reinterpret_cast<float4*>(out + g * row + c0) + vb + k) = make_float4(o0.x, o0.y, o1.x, o1.y);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) q[k][w] = q[k][w + 1];
+                continue;
+            }
             Cv<R> o;
             if (has_psi) {
                 Cv<R> ps;
-                unpack(pp[k], ps);
+                if (psi_mode == 1) unpack(q[k][2], ps);
+                else unpack(sPsi[(i % PSL) * Slot<VP>::PN + (offPs ^ k)], ps);
 #pragma unroll
                 for (int e = 0; e < NC; ++e) {
                     o.re[e] = ps.re[e] + gre * hw[k].re[e] - gim * hw[k].im[e];
@@ -450,12 +580,13 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 }
             }
             const float4 ov = pack(o);
-            *(reinterpret_cast<float4*>(out + g * row + c0) + jv + TPP * k) = ov;
-            if (do_obs) {
-                const Cv<R>& c = q[k][2];
+            *(reinterpret_cast<float4*>(out + g * row + c0) + vb + k) = ov;
+            if constexpr (OBS) {
+                Cv<R> c;
+                unpack(q[k][2], c);
 #pragma unroll
                 for (int e = 0; e < NC; ++e) {
-                    const R fo = f[c0 / 2 + (jv + TPP * k) * NC + e];
+                    const R fo = f[c0 / 2 + (vb + k) * NC + e];
                     const R cr = c.re[e], ci = c.im[e];
                     acc[0] += fo * (cr * cr + ci * ci);
                     acc[1] += fo * (cr * hw[k].re[e] + ci * hw[k].im[e]);
@@ -472,9 +603,11 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             atomicExch(err, 1);
             // let the copies still in flight land before the CTA's shared memory goes away
             for (int p = waited; p < issued; ++p) (void)wait_plane(p);
+            for (int j = waited_p; j < issued_p; ++j)
+                (void)mbar_wait_bounded(&pbars[j % PSL], (uint32_t)((j / PSL) & 1));
         }
     }
-    if (do_obs) {
+    if constexpr (OBS) {
         __shared__ double sh[NT / 32][5];
         const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
@@ -520,8 +653,8 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
     constexpr int EG = 32 / (PPW * VP);                      // entry groups per warp
     constexpr int NPASS = NP / PPW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    // W [pzc][64][VP] float4, rows [pcap + 8] int32, beta [pcap][NP] R
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    // W [pzc][64][VP] float4 (swizzled like the stage kernel's tiles), rows [pcap + 8] int32, beta [pcap][NP] R
     const uint32_t wbytes = (uint32_t)pzc * 64 * VP * 16;
     const uint32_t kbytes = (uint32_t)(pcap + 8) * 4;
     const float4* sW = reinterpret_cast<const float4*>(base);
@@ -529,11 +662,11 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
     __shared__ int abort_sh;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int pcol = blockIdx.x + gridDim.x * blockIdx.z;
-    const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
+    const int pcol = blockIdx.y + gridDim.y * blockIdx.z;    // grid (chunk, tile, z range)
+    const int x0 = (blockIdx.y % ntx) * TX, y0 = (blockIdx.y / ntx) * TY;
     const int z0 = blockIdx.z * pzc;
     const int nzc = min(pzc, nz - z0);
-    const int c0 = blockIdx.y * OCR;
+    const int c0 = blockIdx.x * OCR;
     const int k0 = N.pp_atom_start[pcol], k1 = N.pp_atom_start[pcol + 1];   // the column's slots
     const int e0 = N.pp_seg[k0], e1 = N.pp_seg[k1];
     if (e1 == e0) return;
@@ -571,8 +704,8 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
                 for (; e + EG < hi; e += 2 * EG) {          // two independent entries in flight
                     const R bv0 = sB[(int64_t)e * NP + pi], bv1 = sB[(int64_t)(e + EG) * NP + pi];
                     Cv<R> w0, w1;
-                    unpack(sW[sRow[e] * VP + jj], w0);
-                    unpack(sW[sRow[e + EG] * VP + jj], w1);
+                    unpack(sW[swz<VP>(sRow[e] * VP, jj)], w0);
+                    unpack(sW[swz<VP>(sRow[e + EG] * VP, jj)], w1);
 #pragma unroll
                     for (int u = 0; u < NC; ++u) {
                         a.re[u] += bv0 * w0.re[u]; a.im[u] += bv0 * w0.im[u];
@@ -582,7 +715,7 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
                 if (e < hi) {
                     const R bv0 = sB[(int64_t)e * NP + pi];
                     Cv<R> w0;
-                    unpack(sW[sRow[e] * VP + jj], w0);
+                    unpack(sW[swz<VP>(sRow[e] * VP, jj)], w0);
 #pragma unroll
                     for (int u = 0; u < NC; ++u) { a.re[u] += bv0 * w0.re[u]; a.im[u] += bv0 * w0.im[u]; }
                 }
@@ -602,29 +735,25 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
 
 template <typename R, int VP>
 size_t project_smem(int np, int pcap, int pzc) {
-    return (size_t)pzc * 64 * VP * 16 + (size_t)(pcap + 8) * 4 + (size_t)pcap * np * sizeof(R) + 128;
+    return (size_t)pzc * 64 * VP * 16 + (size_t)(pcap + 8) * 4 + (size_t)pcap * np * sizeof(R) + 1024;
 }
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-template <int NP> struct SlotsFor { static constexpr int value = 4; };
-
 template <typename R, int VP, int NP>
-size_t smem_bytes(int maxs) {
-    constexpr int NSLOT = SlotsFor<NP>::value;
+size_t smem_bytes(int maxs, int nslot) {
     const int npv = NP > 0 ? NP : 1;
-    size_t b = (size_t)NSLOT * Slot<VP>::BYTES;
+    size_t b = (size_t)nslot * Slot<VP>::N * 16 + (size_t)PSL * Slot<VP>::PSI_BYTES;
     if (NP > 0)
         b += (size_t)maxs * npv * VP * 16 + ((size_t)maxs * npv * sizeof(R) + 15) / 16 * 16;
-    return b + 128;
+    return b + 1024;
 }
 
 TmaMaps maps_for(Domain& d, const void* base);
 
 template <typename R, int ORDER, int VP, int NP>
 void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool proj) {
-    constexpr int NSLOT = SlotsFor<NP>::value;
     const TmaState& t = *d.tma;
     const Geo G0 = geo_of(d);
     TGeo<R> G;
@@ -650,15 +779,21 @@ void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool
         N.dV = (R)(d.desc.h * d.desc.h * d.desc.h);
         N.maxs = t.maxs;
     }
-    const size_t smem = smem_bytes<R, VP, NP>(NP > 0 ? t.maxs : 0);
+    const int maxs = NP > 0 ? t.maxs : 0;
+    const int nslot = 4;
+    const size_t smem = smem_bytes<R, VP, NP>(maxs, nslot);
     constexpr int TPP_WIDE = VP == 8 ? 8 : 4;       // one 16-byte vector per thread
     const int tpp = t.tpp == 8 ? TPP_WIDE : 4;
-    auto kern = tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, NSLOT, TPP_WIDE> : k_stage_tma<R, ORDER, VP, NP, NSLOT, 4>;
+    const bool obs = a.obs != nullptr;
+    auto kern = obs ? (tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, 4, TPP_WIDE, true> : k_stage_tma<R, ORDER, VP, NP, 4, 4, true>)
+                    : (tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, 4, TPP_WIDE, false> : k_stage_tma<R, ORDER, VP, NP, 4, 4, false>);
     ensure_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
     N.Pout = nullptr;
     {
         ProfScope ps(d.prof, MLMD_KERNEL_STAGE, d.stream);
-        kern<<<grid, 64 * tpp, smem, d.stream>>>(m.centre, m.xslab, m.yslab, G, static_cast<const R*>(a.psi),
+        const int psi_mode = a.psi == nullptr ? 0 : (a.psi == a.w ? 1 : 2);
+        const CUtensorMap tm_p = psi_mode == 2 ? maps_for(d, a.psi).centre : m.centre;
+        kern<<<grid, 64 * tpp, smem, d.stream>>>(m.centre, m.xslab, m.yslab, tm_p, psi_mode, G,
                                            static_cast<R*>(a.out), static_cast<const R*>(d.V),
                                            static_cast<const R*>(d.fR), a.A, N, (R)a.gamma_re, (R)a.gamma_im, a.obs,
                                            d.err_flag);
@@ -712,7 +847,8 @@ void encode(CUtensorMap* map, const Domain& d, const void* base, uint32_t bx, ui
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = encode_fn()(map, d.c64() ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                              const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             d.tma->vp == 8 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     MLMD_REQUIRE(r == CUDA_SUCCESS, MLMD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 }
@@ -879,12 +1015,12 @@ void tma_build_nl(Domain& d, const double* D_host) {
     t.pcap = (pcap + 3) / 4 * 4;
     size_t sm8 = 0, sm4 = 0;
     if (d.c64()) {
-        sm8 = std::max(np == 4 ? smem_bytes<float, 8, 4>(t.maxs) : smem_bytes<float, 8, 8>(t.maxs),
+        sm8 = std::max(np == 4 ? smem_bytes<float, 8, 4>(t.maxs, 4) : smem_bytes<float, 8, 8>(t.maxs, 4),
                        project_smem<float, 8>(np, t.pcap, t.pzc));
-        sm4 = std::max(np == 4 ? smem_bytes<float, 4, 4>(t.maxs) : smem_bytes<float, 4, 8>(t.maxs),
+        sm4 = std::max(np == 4 ? smem_bytes<float, 4, 4>(t.maxs, 4) : smem_bytes<float, 4, 8>(t.maxs, 4),
                        project_smem<float, 4>(np, t.pcap, t.pzc));
     } else {
-        sm8 = sm4 = std::max(np == 4 ? smem_bytes<double, 8, 4>(t.maxs) : smem_bytes<double, 8, 8>(t.maxs),
+        sm8 = sm4 = std::max(np == 4 ? smem_bytes<double, 8, 4>(t.maxs, 4) : smem_bytes<double, 8, 8>(t.maxs, 4),
                              project_smem<double, 8>(np, t.pcap, t.pzc));
     }
     const size_t kMaxSmem = 200 * 1024;
@@ -935,7 +1071,7 @@ bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done) {
     const bool proj = nl && a.P_out != nullptr;
     const TmaState& t = *d.tma;
     const TmaMaps m = maps_for(d, a.w);
-    dim3 grid((d.desc.n[0] / TX) * (d.desc.n[1] / TY), chunks_of(d), (d.desc.n[2] + t.zc - 1) / t.zc);
+    dim3 grid(chunks_of(d), (d.desc.n[0] / TX) * (d.desc.n[1] / TY), (d.desc.n[2] + t.zc - 1) / t.zc);
     if (proj)
         MLMD_CUDA(cudaMemsetAsync(a.P_out, 0, (size_t)d.nl.n_atoms * d.nl.n_proj * d.ld * d.elem, d.stream));
     if (d.c64()) {
