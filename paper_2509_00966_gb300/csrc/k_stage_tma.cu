@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <type_traits>
@@ -627,6 +628,19 @@ __global__ void __launch_bounds__(64 * TPP, 2)
 }
 
 
+// NP projector values of one entry from shared memory, 16 bytes at a time
+template <typename R, int NP>
+__device__ __forceinline__ void load_beta_s(const R* p, R (&b)[NP]) {
+    constexpr int PER = 16 / (int)sizeof(R);
+#pragma unroll
+    for (int v = 0; v < NP / PER; ++v) {
+        const float4 t = reinterpret_cast<const float4*>(p)[v];
+        const R* tr = reinterpret_cast<const R*>(&t);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) b[v * PER + k] = tr[k];
+    }
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
@@ -649,9 +663,7 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
                                                          int* err) {
     constexpr int OCR = VP * 16 / sizeof(R);
     constexpr int NC = V16<R>::NC;
-    constexpr int PPW = (32 / VP) < NP ? (32 / VP) : NP;    // projectors per warp pass
-    constexpr int EG = 32 / (PPW * VP);                      // entry groups per warp
-    constexpr int NPASS = NP / PPW;
+    constexpr int EG = 32 / VP;                              // entry groups per warp
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     // W [pzc][64][VP] float4 (swizzled like the stage kernel's tiles), rows [pcap + 8] int32, beta [pcap][NP] R
@@ -687,41 +699,48 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
     const bool ok = mbar_wait_bounded(&bar, 0);
     const int T = e1 - e0;
     const int r0 = e0 + (int)(((int64_t)T * warp) / 8), r1 = e0 + (int)(((int64_t)T * (warp + 1)) / 8);
-    const int eg = lane / (PPW * VP), pl = (lane / VP) % PPW, jj = lane % VP;
+    const int eg = lane / VP, jj = lane % VP;
     const int64_t row = 2 * (int64_t)ld;
     if (ok && r1 > r0) {
         for (int k = k0; k < k1; ++k) {
             const int lo = max(r0, N.pp_seg[k]), hi = min(r1, N.pp_seg[k + 1]);
-            if (lo >= hi) continue;
-            const int64_t at = N.pp_atom[k];
+            if (lo >= hi) continue;                  // the same for the whole warp
+            Cv<R> acc[NP];
 #pragma unroll
-            for (int pass = 0; pass < NPASS; ++pass) {
-                const int pi = pass * PPW + pl;
-                Cv<R> a, b2;
+            for (int pi = 0; pi < NP; ++pi)
 #pragma unroll
-                for (int u = 0; u < NC; ++u) { a.re[u] = 0; a.im[u] = 0; b2.re[u] = 0; b2.im[u] = 0; }
-                int e = lo + eg;
-                for (; e + EG < hi; e += 2 * EG) {          // two independent entries in flight
-                    const R bv0 = sB[(int64_t)e * NP + pi], bv1 = sB[(int64_t)(e + EG) * NP + pi];
-                    Cv<R> w0, w1;
-                    unpack(sW[swz<VP>(sRow[e] * VP, jj)], w0);
-                    unpack(sW[swz<VP>(sRow[e + EG] * VP, jj)], w1);
+                for (int u = 0; u < NC; ++u) { acc[pi].re[u] = 0; acc[pi].im[u] = 0; }
+            for (int e = lo + eg; e < hi; e += EG) {
+                const int r = sRow[e];
+                // swizzled row start r*VP + (r mod 8): vector jj sits at that XOR jj
+                const int K = r * VP + (VP == 8 ? (r & 7) : 0);
+                Cv<R> w;
+                unpack(sW[K ^ jj], w);
+                R b[NP];
+                load_beta_s<R, NP>(sB + (int64_t)e * NP, b);
+#pragma unroll
+                for (int pi = 0; pi < NP; ++pi)
 #pragma unroll
                     for (int u = 0; u < NC; ++u) {
-                        a.re[u] += bv0 * w0.re[u]; a.im[u] += bv0 * w0.im[u];
-                        b2.re[u] += bv1 * w1.re[u]; b2.im[u] += bv1 * w1.im[u];
+                        acc[pi].re[u] += b[pi] * w.re[u];
+                        acc[pi].im[u] += b[pi] * w.im[u];
                     }
-                }
-                if (e < hi) {
-                    const R bv0 = sB[(int64_t)e * NP + pi];
-                    Cv<R> w0;
-                    unpack(sW[swz<VP>(sRow[e] * VP, jj)], w0);
+            }
+            // sum the entry groups (lanes jj, jj + VP, ...)
 #pragma unroll
-                    for (int u = 0; u < NC; ++u) { a.re[u] += bv0 * w0.re[u]; a.im[u] += bv0 * w0.im[u]; }
-                }
+            for (int off = VP; off < 32; off <<= 1)
 #pragma unroll
-                for (int u = 0; u < NC; ++u) { a.re[u] += b2.re[u]; a.im[u] += b2.im[u]; }
-                global_add(N.Pout + (at * NP + pi) * row + c0 + jj * (16 / (int)sizeof(R)), pack(a), N.dV);
+                for (int pi = 0; pi < NP; ++pi)
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) {
+                        acc[pi].re[u] += __shfl_xor_sync(0xffffffffu, acc[pi].re[u], off);
+                        acc[pi].im[u] += __shfl_xor_sync(0xffffffffu, acc[pi].im[u], off);
+                    }
+            if (eg == 0) {
+                const int64_t at = N.pp_atom[k];
+#pragma unroll
+                for (int pi = 0; pi < NP; ++pi)
+                    global_add(N.Pout + (at * NP + pi) * row + c0 + jj * (16 / (int)sizeof(R)), pack(acc[pi]), N.dV);
             }
         }
     }
@@ -1097,6 +1116,18 @@ void tma_autotune(Domain& d, const double* Ak) {
     t.tuned = true;
     const bool nl = d.has_nl();
     if (nl && !t.nl_ok) return;
+    // MLMD_STAGE_TILE="vp,tpp" (e.g. "8,4") fixes the shape instead, for
+    // reproducible profiles; ignored unless it names a valid shape here
+    if (const char* fix = std::getenv("MLMD_STAGE_TILE")) {
+        int vp = 0, tpp = 0;
+        if (std::sscanf(fix, "%d,%d", &vp, &tpp) == 2 && (tpp == 4 || (tpp == 8 && vp == 8)) &&
+            ((vp == 8 && t.vp == 8) || (vp == 4 && d.c64() && (t.vp == 4 || t.vp8_ok)))) {
+            t.vp = vp;
+            t.tpp = tpp;
+            t.maps.clear();
+            return;
+        }
+    }
     std::vector<std::pair<int, int>> cand;
     if (t.vp == 8) {
         cand.push_back({8, 4});
