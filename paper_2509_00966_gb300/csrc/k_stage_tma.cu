@@ -53,9 +53,13 @@ struct TmaState {
     int maxs = 0;             // most atoms touching one column
     int32_t* col_start = nullptr;
     int32_t* col_atom = nullptr;
-    int32_t* ent_slot = nullptr;
-    void* ent_beta = nullptr;
-    void* D = nullptr;
+    // scatter-back entries, one 16-byte aligned block per (column, plane):
+    // int32 header [68] = entry offsets of the 64 points (65 values), the
+    // entry count n and n rounded up to 4; then the slots [n4] int32, then
+    // beta * D [n][NP] in the working real type
+    unsigned char* sblk = nullptr;
+    int64_t* sblk_off = nullptr;      // [ncols * zc + 1] byte offsets
+    int scap = 0;                     // largest block, bytes
     // projection tables: half-height columns of PZC planes, entries slot-major
     int pzc = 0;              // planes per projection column
     int pcap = 0;             // most entries of one projection column, a multiple of 4
@@ -180,12 +184,11 @@ __device__ __forceinline__ int swz(int o, int v) {
 
 // Nonlocal tables of the fused path (see the file comment).
 template <typename R> struct TNl {
-    const int32_t* pstart;     // [N_g + 1] per-point entry ranges
-    const int32_t* slot;       // [n_list] slot of each entry's atom within the point's column
-    const R* beta;             // [n_list][NP] projector values times D (scatter-back)
+    const unsigned char* sblk; // scatter-back entry blocks (see TmaState)
+    const int64_t* sblk_off;
+    int scap;
     const int32_t* col_start;  // [ncols + 1]
     const int32_t* col_atom;   // global atom ids of each column, ascending
-    const R* D;                // [n_atoms][NP]
     const R* Pin;              // <b|w>: [n_atoms][NP] rows of 2 ld reals
     R* Pout;                   // <b|out> accumulated (zeroed by the caller), or null
     // projection of the output: projection columns (PZC planes), entries
@@ -220,6 +223,25 @@ __device__ __forceinline__ void global_add(double* p, float4 v, double s) {
     atomicAdd(p + 1, s * d.y);
 }
 
+// NP projector values of one entry from shared memory, 16 bytes at a time
+template <typename R, int NP>
+__device__ __forceinline__ void load_beta_s(const R* p, R (&b)[NP]) {
+    constexpr int PER = 16 / (int)sizeof(R);
+#pragma unroll
+    for (int v = 0; v < NP / PER; ++v) {
+        const float4 t = reinterpret_cast<const float4*>(p)[v];
+        const R* tr = reinterpret_cast<const R*>(&t);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) b[v * PER + k] = tr[k];
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // packed pairs of FP32 (Blackwell f32x2 arithmetic): one complex64 value
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -249,7 +271,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     float4* ring = reinterpret_cast<float4*>(smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u));
     float4* sPsi = ring + NSLOT * Slot<VP>::N;      // [PSL][TY][TX][VP] psi tiles
     float4* sP = sPsi + PSL * Slot<VP>::PN;         // [maxs][NP][VP] staged <b|w>
-    R* sD = reinterpret_cast<R*>(sP + N.maxs * NPV * VP);   // [maxs][NP]
+    unsigned char* sE = reinterpret_cast<unsigned char*>(sP + N.maxs * NPV * VP);   // [NSLOT][scap] entry blocks
     __shared__ __align__(8) uint64_t bars[NSLOT];
     __shared__ __align__(8) uint64_t pbars[PSL];
     __shared__ R sA[4];
@@ -294,10 +316,6 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             const int64_t a = N.col_atom[cs + s];
             sP[idx] = __ldg(reinterpret_cast<const float4*>(N.Pin + (a * NPV + i) * 2 * G.ld + c0) + jj);
         }
-        for (int idx = tid; idx < na * NPV; idx += NT) {
-            const int s = idx / NPV, i = idx - s * NPV;
-            sD[idx] = N.D[(int64_t)N.col_atom[cs + s] * NPV + i];
-        }
     }
     __syncthreads();
 
@@ -306,7 +324,17 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         const int zz = ((z0 - 2 + p) % G.nz + G.nz) % G.nz;
         float4* d = ring + s * Slot<VP>::N;
         uint64_t* b = &bars[s];
-        mbar_expect_tx(b, Slot<VP>::BYTES);
+        // the scatter entries of computed plane p - 2 travel with w plane p
+        const int j = p - 2;
+        uint32_t eb = 0;
+        int64_t eo = 0;
+        if (NP > 0 && j >= 0 && j < nzc) {
+            const int64_t blk = (int64_t)col * G.zc + j;
+            eo = N.sblk_off[blk];
+            eb = (uint32_t)(N.sblk_off[blk + 1] - eo);
+        }
+        mbar_expect_tx(b, Slot<VP>::BYTES + eb);
+        if (eb) bulk_g2s(sE + (size_t)s * N.scap, N.sblk + eo, eb, b);
         tma_load_4d(d + Slot<VP>::C, &tm_c, c0, x0, y0, zz, b);
         tma_load_4d(d + Slot<VP>::XM, &tm_x, c0, (x0 - 2 + G.nx) % G.nx, y0, zz, b);
         tma_load_4d(d + Slot<VP>::XP, &tm_x, c0, (x0 + TX) % G.nx, y0, zz, b);
@@ -372,25 +400,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     const int64_t plane_stride = (int64_t)G.nx * G.ny;
     int64_t g = (x0 + lx) + (int64_t)G.nx * (y0 + ly) + plane_stride * z0;
     const int64_t row = 2 * (int64_t)G.ld;
-    // nonlocal entry range of this thread's point, one plane ahead
-    int e0n = 0, e1n = 0;
-    if (NP > 0 && nzc > 0) { e0n = N.pstart[g]; e1n = N.pstart[g + 1]; }
     R vnext = nzc > 0 ? V[g] : (R)0;       // V one plane ahead
     for (int i = 0; i < nzc && !aborted0; ++i, g += plane_stride) {
         // per-point global loads first, so that they overlap the plane wait
         // and the shared-memory stencil
         const R vv = vnext;
         if (i + 1 < nzc) vnext = V[g + plane_stride];
-        const int e0 = e0n, e1 = e1n;
-        int sf = 0;
-        R bf[NPV];
-        if (NP > 0) {
-            if (i + 1 < nzc) { e0n = N.pstart[g + plane_stride]; e1n = N.pstart[g + plane_stride + 1]; }
-            if (e0 < e1) {      // the first entry's slot and beta * D
-                sf = N.slot[e0];
-                load_beta<R, NPV>(N.beta + (int64_t)e0 * NPV, bf);
-            }
-        }
         // plane z+2 (p = i+4) must have landed
         ok = wait_plane(i + 4);
         if (!ok) abort_sh = 1;
@@ -512,16 +527,15 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         }
         }
         if (NP > 0) {           // scatter-back: sum_(a,i) b_ai(r) D_ai <b_ai|w>
+            const unsigned char* eb = sE + (size_t)((i + 2) % NSLOT) * N.scap;
+            const int32_t* hdr = reinterpret_cast<const int32_t*>(eb);
+            const int32_t* eslot = hdr + 68;
+            const R* ebd = reinterpret_cast<const R*>(eb + 272 + 4 * hdr[66]);
+            const int e0 = hdr[pt], e1 = hdr[pt + 1];
             for (int e = e0; e < e1; ++e) {
-                int s = sf;
+                const int s = eslot[e];
                 R b[NPV];
-                if (e == e0) {
-#pragma unroll
-                    for (int pi = 0; pi < NPV; ++pi) b[pi] = bf[pi];
-                } else {
-                    s = N.slot[e];
-                    load_beta<R, NPV>(N.beta + (int64_t)e * NPV, b);   // beta * D
-                }
+                load_beta_s<R, NPV>(ebd + (int64_t)e * NPV, b);   // beta * D
 #pragma unroll
                 for (int pi = 0; pi < NPV; ++pi) {
                     const R bd = b[pi];
@@ -628,24 +642,6 @@ __global__ void __launch_bounds__(64 * TPP, 2)
 }
 
 
-// NP projector values of one entry from shared memory, 16 bytes at a time
-template <typename R, int NP>
-__device__ __forceinline__ void load_beta_s(const R* p, R (&b)[NP]) {
-    constexpr int PER = 16 / (int)sizeof(R);
-#pragma unroll
-    for (int v = 0; v < NP / PER; ++v) {
-        const float4 t = reinterpret_cast<const float4*>(p)[v];
-        const R* tr = reinterpret_cast<const R*>(&t);
-#pragma unroll
-        for (int k = 0; k < PER; ++k) b[v * PER + k] = tr[k];
-    }
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
 
 // <b|W> for every atom, by projection columns (an 8 x 8 tile of points, one
 // orbital chunk, PZC planes).  Thread 0 brings the column's W planes (one
@@ -760,12 +756,15 @@ size_t project_smem(int np, int pcap, int pzc) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// dynamic shared memory per CTA that lets two CTAs share an SM (228 KB,
+// less 1 KB the runtime keeps per CTA)
+constexpr size_t kTwoCtaSmem = 113 * 1024;
+
 template <typename R, int VP, int NP>
-size_t smem_bytes(int maxs, int nslot) {
+size_t smem_bytes(int maxs, int nslot, int scap) {
     const int npv = NP > 0 ? NP : 1;
     size_t b = (size_t)nslot * Slot<VP>::N * 16 + (size_t)PSL * Slot<VP>::PSI_BYTES;
-    if (NP > 0)
-        b += (size_t)maxs * npv * VP * 16 + ((size_t)maxs * npv * sizeof(R) + 15) / 16 * 16;
+    if (NP > 0) b += (size_t)maxs * npv * VP * 16 + (size_t)nslot * scap;
     return b + 1024;
 }
 
@@ -782,12 +781,11 @@ void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool
     G.zc = t.zc;
     TNl<R> N{};
     if (NP > 0) {
-        N.pstart = d.nl.pstart;
-        N.slot = t.ent_slot;
-        N.beta = static_cast<const R*>(t.ent_beta);
+        N.sblk = t.sblk;
+        N.sblk_off = t.sblk_off;
+        N.scap = t.scap;
         N.col_start = t.col_start;
         N.col_atom = t.col_atom;
-        N.D = static_cast<const R*>(t.D);
         N.Pin = static_cast<const R*>(a.P);
         N.Pout = proj ? static_cast<R*>(a.P_out) : nullptr;
         N.pp_seg = t.pp_seg;
@@ -799,13 +797,20 @@ void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool
         N.maxs = t.maxs;
     }
     const int maxs = NP > 0 ? t.maxs : 0;
-    const int nslot = 4;
-    const size_t smem = smem_bytes<R, VP, NP>(maxs, nslot);
+    // five w slots (a deeper prefetch) when two CTAs still fit on an SM
+    const int scap = NP > 0 ? t.scap : 0;
+    const int nslot = smem_bytes<R, VP, NP>(maxs, 5, scap) <= kTwoCtaSmem ? 5 : 4;
+    const size_t smem = smem_bytes<R, VP, NP>(maxs, nslot, scap);
     constexpr int TPP_WIDE = VP == 8 ? 8 : 4;       // one 16-byte vector per thread
     const int tpp = t.tpp == 8 ? TPP_WIDE : 4;
     const bool obs = a.obs != nullptr;
-    auto kern = obs ? (tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, 4, TPP_WIDE, true> : k_stage_tma<R, ORDER, VP, NP, 4, 4, true>)
-                    : (tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, 4, TPP_WIDE, false> : k_stage_tma<R, ORDER, VP, NP, 4, 4, false>);
+    decltype(&k_stage_tma<R, ORDER, VP, NP, 4, 4, false>) kern;
+    if (nslot == 5)
+        kern = obs ? (tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, 5, TPP_WIDE, true> : k_stage_tma<R, ORDER, VP, NP, 5, 4, true>)
+                   : (tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, 5, TPP_WIDE, false> : k_stage_tma<R, ORDER, VP, NP, 5, 4, false>);
+    else
+        kern = obs ? (tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, 4, TPP_WIDE, true> : k_stage_tma<R, ORDER, VP, NP, 4, 4, true>)
+                   : (tpp == 8 ? k_stage_tma<R, ORDER, VP, NP, 4, TPP_WIDE, false> : k_stage_tma<R, ORDER, VP, NP, 4, 4, false>);
     ensure_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
     N.Pout = nullptr;
     {
@@ -918,11 +923,14 @@ void tma_release(Domain& d) {
 void tma_build_nl(Domain& d, const double* D_host) {
     if (!d.tma || !d.tma->ok) return;
     TmaState& t = *d.tma;
-    for (void* p : {(void*)t.col_start, (void*)t.col_atom, (void*)t.ent_slot, t.ent_beta, t.D, (void*)t.pp_seg,
+    for (void* p : {(void*)t.col_start, (void*)t.col_atom, (void*)t.sblk, (void*)t.sblk_off, (void*)t.pp_seg,
                     (void*)t.pp_atom_start, (void*)t.pp_atom, (void*)t.pp_key, t.pp_beta})
         if (p) d.mem.put(p);
-    t.col_start = t.col_atom = t.ent_slot = t.pp_seg = t.pp_atom_start = t.pp_atom = t.pp_key = nullptr;
-    t.ent_beta = t.D = t.pp_beta = nullptr;
+    t.col_start = t.col_atom = t.pp_seg = t.pp_atom_start = t.pp_atom = t.pp_key = nullptr;
+    t.sblk = nullptr;
+    t.sblk_off = nullptr;
+    t.pp_beta = nullptr;
+    t.scap = 0;
     t.nl_ok = false;
     t.maxs = 0;
     const Nonlocal& nl = d.nl;
@@ -975,10 +983,46 @@ void tma_build_nl(Domain& d, const double* D_host) {
         t.maxs = std::max<int>(t.maxs, (int)catoms[c].size());
         col_atom.insert(col_atom.end(), catoms[c].begin(), catoms[c].end());
     }
-    std::vector<unsigned char> Dr((size_t)nl.n_atoms * np * rs);
-    for (int64_t k = 0; k < (int64_t)nl.n_atoms * np; ++k) {
-        if (rs == 4) reinterpret_cast<float*>(Dr.data())[k] = (float)D_host[k];
-        else reinterpret_cast<double*>(Dr.data())[k] = D_host[k];
+    // scatter-back blocks, one per (column, plane) in column-major order:
+    // header [68] int32 (point offsets 0..64, n, n4, 0), slots [n4], beta * D [n][np]
+    std::vector<unsigned char> sblk;
+    std::vector<int64_t> sblk_off((size_t)t.ncols * t.zc + 1, 0);
+    {
+        const int nzch = (d.desc.n[2] + t.zc - 1) / t.zc;
+        for (int zc_i = 0; zc_i < nzch; ++zc_i)
+            for (int tile = 0; tile < ntiles; ++tile)
+                for (int iz = 0; iz < t.zc; ++iz) {
+                    const int64_t blk = (int64_t)(tile + ntiles * zc_i) * t.zc + iz;
+                    const int z = zc_i * t.zc + iz;
+                    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+                    int32_t hdr[68] = {0};
+                    std::vector<int32_t> sl;
+                    std::vector<unsigned char> bd;
+                    if (z < d.desc.n[2])
+                        for (int pt = 0; pt < 64; ++pt) {
+                            hdr[pt] = (int32_t)sl.size();
+                            const int64_t g = (x0 + pt % TX) + (int64_t)nx * (y0 + pt / TX) + (int64_t)nx * ny * z;
+                            for (int32_t e = pstart[g]; e < pstart[g + 1]; ++e) {
+                                sl.push_back(ent_slot[e]);
+                                bd.insert(bd.end(), ent_beta.begin() + (size_t)e * np * rs,
+                                          ent_beta.begin() + (size_t)(e + 1) * np * rs);
+                            }
+                        }
+                    const int n = (int)sl.size(), n4 = (n + 3) / 4 * 4;
+                    for (int pt = (z < d.desc.n[2] ? 64 : 0); pt <= 64; ++pt) hdr[pt] = n;
+                    hdr[65] = n;
+                    hdr[66] = n4;
+                    sl.resize(n4, 0);
+                    bd.resize((bd.size() + 15) / 16 * 16, 0);
+                    sblk_off[blk] = (int64_t)sblk.size();
+                    const unsigned char* hp = reinterpret_cast<const unsigned char*>(hdr);
+                    sblk.insert(sblk.end(), hp, hp + sizeof(hdr));
+                    const unsigned char* sp = reinterpret_cast<const unsigned char*>(sl.data());
+                    sblk.insert(sblk.end(), sp, sp + sl.size() * sizeof(int32_t));
+                    sblk.insert(sblk.end(), bd.begin(), bd.end());
+                    t.scap = std::max<int>(t.scap, (int)(sblk.size() - sblk_off[blk]));
+                }
+        sblk_off[(size_t)t.ncols * t.zc] = (int64_t)sblk.size();
     }
     // projection tables: projection columns of pzc planes, entries ordered by
     // (slot, plane, point); slots number a column's atoms in ascending order
@@ -1034,12 +1078,12 @@ void tma_build_nl(Domain& d, const double* D_host) {
     t.pcap = (pcap + 3) / 4 * 4;
     size_t sm8 = 0, sm4 = 0;
     if (d.c64()) {
-        sm8 = std::max(np == 4 ? smem_bytes<float, 8, 4>(t.maxs, 4) : smem_bytes<float, 8, 8>(t.maxs, 4),
+        sm8 = std::max(np == 4 ? smem_bytes<float, 8, 4>(t.maxs, 4, t.scap) : smem_bytes<float, 8, 8>(t.maxs, 4, t.scap),
                        project_smem<float, 8>(np, t.pcap, t.pzc));
-        sm4 = std::max(np == 4 ? smem_bytes<float, 4, 4>(t.maxs, 4) : smem_bytes<float, 4, 8>(t.maxs, 4),
+        sm4 = std::max(np == 4 ? smem_bytes<float, 4, 4>(t.maxs, 4, t.scap) : smem_bytes<float, 4, 8>(t.maxs, 4, t.scap),
                        project_smem<float, 4>(np, t.pcap, t.pzc));
     } else {
-        sm8 = sm4 = std::max(np == 4 ? smem_bytes<double, 8, 4>(t.maxs, 4) : smem_bytes<double, 8, 8>(t.maxs, 4),
+        sm8 = sm4 = std::max(np == 4 ? smem_bytes<double, 8, 4>(t.maxs, 4, t.scap) : smem_bytes<double, 8, 8>(t.maxs, 4, t.scap),
                              project_smem<double, 8>(np, t.pcap, t.pzc));
     }
     const size_t kMaxSmem = 200 * 1024;
@@ -1052,15 +1096,9 @@ void tma_build_nl(Domain& d, const double* D_host) {
     }
     t.col_start = (int32_t*)d.mem.get(sizeof(int32_t) * col_start.size());
     t.col_atom = (int32_t*)d.mem.get(sizeof(int32_t) * std::max<size_t>(col_atom.size(), 1));
-    t.ent_slot = (int32_t*)d.mem.get(sizeof(int32_t) * ent_slot.size());
-    t.ent_beta = d.mem.get(ent_beta.size());
-    t.D = d.mem.get(Dr.size());
     MLMD_CUDA(cudaMemcpyAsync(t.col_start, col_start.data(), sizeof(int32_t) * col_start.size(), cudaMemcpyHostToDevice, d.stream));
     if (!col_atom.empty())
         MLMD_CUDA(cudaMemcpyAsync(t.col_atom, col_atom.data(), sizeof(int32_t) * col_atom.size(), cudaMemcpyHostToDevice, d.stream));
-    MLMD_CUDA(cudaMemcpyAsync(t.ent_slot, ent_slot.data(), sizeof(int32_t) * ent_slot.size(), cudaMemcpyHostToDevice, d.stream));
-    MLMD_CUDA(cudaMemcpyAsync(t.ent_beta, ent_beta.data(), ent_beta.size(), cudaMemcpyHostToDevice, d.stream));
-    MLMD_CUDA(cudaMemcpyAsync(t.D, Dr.data(), Dr.size(), cudaMemcpyHostToDevice, d.stream));
     auto upload = [&](const void* src, size_t bytes) {
         void* p = d.mem.get(std::max<size_t>(bytes, 16));
         if (bytes) MLMD_CUDA(cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, d.stream));
@@ -1071,6 +1109,8 @@ void tma_build_nl(Domain& d, const double* D_host) {
     t.pp_atom = (int32_t*)upload(pp_atom.data(), sizeof(int32_t) * pp_atom.size());
     t.pp_key = (int32_t*)upload(pp_key.data(), sizeof(int32_t) * pp_key.size());
     t.pp_beta = upload(pp_beta.data(), pp_beta.size());
+    t.sblk = (unsigned char*)upload(sblk.data(), sblk.size());
+    t.sblk_off = (int64_t*)upload(sblk_off.data(), sizeof(int64_t) * sblk_off.size());
     MLMD_CUDA(cudaStreamSynchronize(d.stream));
     t.nl_ok = true;
 }

@@ -95,6 +95,26 @@ def test_tma_stage_path(precision, n, n_orb, order):
     assert np.max(np.abs(out2 - out)) <= tol
 
 
+@pytest.mark.parametrize("tile,precision,n_proj,order", [
+    ("8,4", "c64", 4, 4), ("8,8", "c64", 4, 4), ("4,4", "c64", 4, 4),
+    ("8,4", "c64", 8, 2), ("8,8", "c64", 8, 4), ("4,4", "c64", 8, 4),
+    ("8,4", "c128", 4, 4), ("8,8", "c128", 8, 2),
+])
+def test_stage_tile_shapes(tile, precision, n_proj, order, monkeypatch):
+    """Every tile shape of the TMA stage kernel (orbital chunk of 8 or 4
+    16-byte vectors; 4 or 8 threads per grid point), fixed through
+    MLMD_STAGE_TILE instead of the timing autotuner, on a grid with several
+    tiles, z ranges and projection columns (the projection of the output is
+    a separate kernel), against the oracle."""
+    monkeypatch.setenv("MLMD_STAGE_TILE", tile)
+    spec = small_spec(precision=precision, n=(16, 16, 20), n_orb=48, fd_order=order, steps=8, n_atoms=7,
+                      n_proj=n_proj, r_cut=2.6)
+    tol = 1e-12 if precision == "c128" else 1e-5
+    out, obs, ref, robs = _run_both(spec)
+    assert np.max(np.abs(out - ref)) <= tol
+    _check_obs(obs, robs, 1e-11 if precision == "c128" else 1e-5)
+
+
 def test_projector_lists_bit_exact():
     for spec in [small_spec(n_atoms=9, r_cut=1.7), inputs.config("c1", n_orb=8, n_steps=1),
                  inputs.config("c2", n_orb=8, n_steps=1), inputs.config("c4", n_orb=8, n_steps=1)]:
