@@ -47,6 +47,8 @@ def _args():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    p.add_argument("--reorth", nargs=3, metavar=("N", "N_ORB", "MODE"),
+                   help="time Cholesky re-orthonormalisations of an N^3 x N_ORB complex64 domain in gemm MODE")
     p.add_argument("--gram", nargs=3, metavar=("N", "N_ORB", "MODE"),
                    help="time the overlap (Gram) GEMM of an N^3 x N_ORB complex64 domain in gemm MODE")
     p.add_argument("--suite", action="store_true",
@@ -459,12 +461,33 @@ def run_gram(args):
     d.close()
 
 
+def run_reorth(args):
+    """Time mlmd_reorthonormalize (FP64 Cholesky on the device, Gram and
+    update GEMMs in the given gemm mode) on an N^3 x N_ORB complex64 domain
+    of seeded random orbitals; reports ms per call and max |S - I| after."""
+    import torch
+    from paper_2509_00966_gb300 import build, mlmd
+    build.build()
+    n, no, mode = int(args.reorth[0]), int(args.reorth[1]), args.reorth[2]
+    h = 0.35
+    d = mlmd.Domain((n, n, n), h, no, 4, "c64", gemm_mode=mode)
+    d.set_orbitals(_device_orbitals(n ** 3, no, h ** 3, 2, torch.complex64))
+    d.reorthonormalize("chol")
+    ms, _ = _timed(lambda: d.reorthonormalize("chol"), reps=3)
+    S = d.overlap()
+    print(json.dumps({"kernel": "reorthonormalize(chol)", "grid": n, "n_orb": no, "mode": mode, "ms": ms,
+                      "max_abs_S_minus_I": float(np.abs(S - np.eye(no)).max())}), flush=True)
+    d.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
     elif args.gram:
         run_gram(args)
+    elif args.reorth:
+        run_reorth(args)
     elif args.suite:
         run_suite(args)
     else:
