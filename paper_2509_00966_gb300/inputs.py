@@ -87,17 +87,24 @@ def _grid_coords(n, h):
 
 def gaussian_wells(n, h, centres, depth, width):
     """V(r) = -sum_w U_w exp(-d^2 / (2 sigma^2)), d summed over the 27 nearest
-    periodic images so that V is periodic.  Returns float64 [N_g]."""
-    r = _grid_coords(n, h)
+    periodic images so that V is periodic.  Returns float64 [N_g].
+
+    The image set is the product {-1, 0, 1}^3, so each well's sum factorises
+    into three one-dimensional periodic sums, g_x(x) g_y(y) g_z(z), and V is
+    one contraction over the wells (x fastest in the result)."""
+    n = tuple(int(v) for v in n)
+    centres = np.asarray(centres, dtype=np.float64).reshape(-1, 3)
+    depth = np.asarray(depth, dtype=np.float64).reshape(-1)
+    if len(centres) == 0:
+        return np.zeros(n[0] * n[1] * n[2])
     L = np.array(n, dtype=np.float64) * h
-    V = np.zeros(r.shape[0])
-    for c, U in zip(np.asarray(centres), np.asarray(depth)):
-        for sx in (-1, 0, 1):
-            for sy in (-1, 0, 1):
-                for sz in (-1, 0, 1):
-                    d = r - (c + np.array([sx, sy, sz]) * L)
-                    V -= U * np.exp(-np.einsum("ij,ij->i", d, d) / (2.0 * width * width))
-    return V
+    g = []
+    for ax in range(3):
+        x = np.arange(n[ax], dtype=np.float64) * h                         # [n_ax]
+        d = x[None, None, :] - (centres[:, ax][:, None, None] + np.array([-1.0, 0.0, 1.0])[None, :, None] * L[ax])
+        g.append(np.exp(-d * d / (2.0 * width * width)).sum(axis=1))      # [wells, n_ax]
+    V = -np.einsum("w,wz,wy,wx->zyx", depth, g[2], g[1], g[0], optimize=True)
+    return np.ascontiguousarray(V).reshape(-1)
 
 
 def random_orbitals(n_grid, n_orb, dV, seed, dtype=np.complex128):
