@@ -1,7 +1,10 @@
 // Batched form: many uneven DC domains (Sec. V.A.1) stepped together on one
 // GPU.  One time step of all domains is captured once as a CUDA graph; the
 // graph reads each domain's vector potential from a device table through a
-// device step counter, so the same graph is replayed for every step.
+// device step counter, so the same graph is replayed for every step.  The
+// domains are spread over kBranches parallel branches of the graph (forked
+// after the step counter is read, joined before it advances), so kernels of
+// different domains can run side by side and fill each other's tails.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -10,6 +13,8 @@
 
 namespace mlmd {
 namespace {
+
+constexpr int kBranches = 8;
 
 // A_cur[d] = A_all[d][ctr]
 __global__ void k_batch_begin(int n_dom, int n_steps, const double* __restrict__ A_all, const int* __restrict__ ctr,
@@ -105,27 +110,42 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         // default stream cannot be captured), ordered after the caller's
         // stream by an event and joined back the same way.
         cudaStream_t cap = nullptr;
-        cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+        cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
+        const int nbr = std::min(nd, kBranches);
+        std::vector<cudaStream_t> br(nbr, nullptr);
+        std::vector<cudaEvent_t> ev_join(nbr, nullptr);
+        struct Restore {
+            std::vector<mlmd_domain*>& ds;
+            cudaStream_t orig;
+            cudaStream_t& cap;
+            std::vector<cudaStream_t>& br;
+            std::vector<cudaEvent_t>& joins;
+            cudaEvent_t &a, &b, &f;
+            ~Restore() {
+                for (auto* d : ds) { d->stream = orig; d->mem.stream = orig; }
+                if (cap) (void)cudaStreamSynchronize(cap);
+                for (auto s : br) if (s) (void)cudaStreamDestroy(s);
+                for (auto e : joins) if (e) (void)cudaEventDestroy(e);
+                if (cap) (void)cudaStreamDestroy(cap);
+                if (a) (void)cudaEventDestroy(a);
+                if (b) (void)cudaEventDestroy(b);
+                if (f) (void)cudaEventDestroy(f);
+            }
+        } restore{b->doms, st, cap, br, ev_join, ev_in, ev_out, ev_fork};
         MLMD_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         MLMD_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
         MLMD_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
-        struct Restore {
-            std::vector<mlmd_domain*>& ds;
-            cudaStream_t orig, cap;
-            cudaEvent_t a, b;
-            ~Restore() {
-                for (auto* d : ds) { d->stream = orig; d->mem.stream = orig; }
-                (void)cudaStreamSynchronize(cap);
-                (void)cudaStreamDestroy(cap);
-                (void)cudaEventDestroy(a);
-                (void)cudaEventDestroy(b);
-            }
-        } restore{b->doms, st, cap, ev_in, ev_out};
+        MLMD_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        for (int k = 0; k < nbr; ++k) {
+            MLMD_CUDA(cudaStreamCreateWithFlags(&br[k], cudaStreamNonBlocking));
+            MLMD_CUDA(cudaEventCreateWithFlags(&ev_join[k], cudaEventDisableTiming));
+        }
         std::vector<uint64_t> before;
         std::vector<bool> prof_on;
-        for (auto* d : b->doms) {
-            d->stream = cap;
-            d->mem.stream = cap;
+        for (int i = 0; i < nd; ++i) {
+            mlmd_domain* d = b->doms[i];
+            d->stream = br[i % nbr];
+            d->mem.stream = br[i % nbr];
             before.push_back(d->launches);
             prof_on.push_back(d->prof.on);
             d->prof.on = false;   // no timing events inside the graph
@@ -135,8 +155,14 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         MLMD_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         try {
             k_batch_begin<<<(nd * 3 + 255) / 256, 256, 0, cap>>>(nd, n_steps, A_all, ctr, A_cur);
+            MLMD_CUDA(cudaEventRecord(ev_fork, cap));
+            for (int k = 0; k < nbr; ++k) MLMD_CUDA(cudaStreamWaitEvent(br[k], ev_fork, 0));
             for (int i = 0; i < nd; ++i)
                 step_full(*b->doms[i], A_cur + 3 * i, obs_out ? obs_cur + 5 * i : nullptr);
+            for (int k = 0; k < nbr; ++k) {
+                MLMD_CUDA(cudaEventRecord(ev_join[k], br[k]));
+                MLMD_CUDA(cudaStreamWaitEvent(cap, ev_join[k], 0));
+            }
             k_batch_end<<<1, 256, 0, cap>>>(nd, n_steps, obs_cur, ctr, obs_all);
         } catch (...) {
             cudaGraph_t g = nullptr;

@@ -168,7 +168,8 @@ GeoR<R> make_geo_r(const Domain& d) {
 // Launch: grid (ceil(nx*nv/256), ny, nz), 256 threads; thread t of a block
 // row covers point x = t / nv of line (y, z) and 16-byte vector j = t % nv.
 // ---------------------------------------------------------------------------
-template <typename R, int ORDER, bool NL, bool OBS, bool HAS_PSI>
+// NLP: projectors per atom of the scatter-back (0: no nonlocal term, 4 or 8)
+template <typename R, int ORDER, int NLP, bool OBS, bool HAS_PSI>
 __global__ void __launch_bounds__(256) k_stage(GeoR<R> G, const R* __restrict__ w, const R* psi, R* out,
                                                const R* __restrict__ V, const R* __restrict__ f,
                                                const double* __restrict__ Ak,
@@ -229,19 +230,37 @@ __global__ void __launch_bounds__(256) k_stage(GeoR<R> G, const R* __restrict__ 
             hw.re[k] = lap.re[k] + diag * c.re[k] + gi;
             hw.im[k] = lap.im[k] + diag * c.im[k] - gr;
         }
-        if (NL) {
+        if constexpr (NLP > 0) {
+            // EU entries at a time: their atoms, beta * D and projection rows
+            // are all requested before any is used
+            constexpr int EU = NLP == 4 ? 2 : 1;
             const int e0 = pstart[g], e1 = pstart[g + 1];
-            for (int e = e0; e < e1; ++e) {
-                const int a = patom[e];
-                for (int i = 0; i < n_proj; ++i) {
-                    const R bd = pbd[(int64_t)e * n_proj + i];
-                    const Cx<R> pv = ldg_c(rowp(P, (int64_t)a * n_proj + i, G.ld, j));
+            for (int e = e0; e < e1; e += EU) {
+                int a[EU];
+                R bd[EU][NLP];
+                Cx<R> pv[EU][NLP];
 #pragma unroll
-                    for (int k = 0; k < NC; ++k) {
-                        hw.re[k] += bd * pv.re[k];
-                        hw.im[k] += bd * pv.im[k];
+                for (int u = 0; u < EU; ++u) a[u] = e + u < e1 ? patom[e + u] : -1;
+#pragma unroll
+                for (int u = 0; u < EU; ++u)
+                    if (a[u] >= 0) {
+#pragma unroll
+                        for (int i = 0; i < NLP; ++i) {
+                            bd[u][i] = pbd[(int64_t)(e + u) * NLP + i];
+                            pv[u][i] = ldg_c(rowp(P, (int64_t)a[u] * NLP + i, G.ld, j));
+                        }
                     }
-                }
+#pragma unroll
+                for (int u = 0; u < EU; ++u)
+                    if (a[u] >= 0) {
+#pragma unroll
+                        for (int i = 0; i < NLP; ++i)
+#pragma unroll
+                            for (int k = 0; k < NC; ++k) {
+                                hw.re[k] += bd[u][i] * pv[u][i].re[k];
+                                hw.im[k] += bd[u][i] * pv[u][i].im[k];
+                            }
+                    }
             }
         }
         Cx<R> o;
@@ -295,12 +314,15 @@ void stage_dispatch(Domain& d, const StageArgs& a, dim3 grid) {
     k_stage<R, ORDER, NLv, OBSv, HPv><<<grid, 256, 0, d.stream>>>(                                   \
         G, w, psi, out, V, f, a.A, d.nl.pstart, d.nl.patom, pbd, P, d.nl.n_proj, (R)a.gamma_re,     \
         (R)a.gamma_im, a.obs)
-    if (nl) {
-        if (obs) { if (hp) MLMD_STAGE(true, true, true); else MLMD_STAGE(true, true, false); }
-        else { if (hp) MLMD_STAGE(true, false, true); else MLMD_STAGE(true, false, false); }
+    if (nl && d.nl.n_proj == 4) {
+        if (obs) { if (hp) MLMD_STAGE(4, true, true); else MLMD_STAGE(4, true, false); }
+        else { if (hp) MLMD_STAGE(4, false, true); else MLMD_STAGE(4, false, false); }
+    } else if (nl) {
+        if (obs) { if (hp) MLMD_STAGE(8, true, true); else MLMD_STAGE(8, true, false); }
+        else { if (hp) MLMD_STAGE(8, false, true); else MLMD_STAGE(8, false, false); }
     } else {
-        if (obs) { if (hp) MLMD_STAGE(false, true, true); else MLMD_STAGE(false, true, false); }
-        else { if (hp) MLMD_STAGE(false, false, true); else MLMD_STAGE(false, false, false); }
+        if (obs) { if (hp) MLMD_STAGE(0, true, true); else MLMD_STAGE(0, true, false); }
+        else { if (hp) MLMD_STAGE(0, false, true); else MLMD_STAGE(0, false, false); }
     }
 #undef MLMD_STAGE
 }

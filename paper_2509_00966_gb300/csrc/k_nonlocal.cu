@@ -248,21 +248,32 @@ __global__ void __launch_bounds__(128) k_project(const R* __restrict__ w, int ld
 #pragma unroll
         for (int k = 0; k < 2 * NC; ++k) acc[i][k] = 0;
     if (j < nv) {
-        for (int64_t q = q0; q < q1; ++q) {
-            const R* row = w + ((int64_t)idx[q] * ld + (int64_t)j * NC) * 2;
-            R v[2 * NC];
-            if (NC == 2) {
-                const float4 t = __ldg(reinterpret_cast<const float4*>(row));
-                v[0] = t.x; v[1] = t.y; v[2 % (2 * NC)] = t.z; v[3 % (2 * NC)] = t.w;
-            } else {
-                const double2 t = __ldg(reinterpret_cast<const double2*>(row));
-                v[0] = t.x; v[1] = t.y;
+        // two points at a time: both rows and both beta vectors are in
+        // flight before either is used
+        for (int64_t q = q0; q < q1; q += 2) {
+            const bool two = q + 1 < q1;
+            R v[2][2 * NC], b[2][NP];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (u == 1 && !two) break;
+                const R* row = w + ((int64_t)idx[q + u] * ld + (int64_t)j * NC) * 2;
+                if (NC == 2) {
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(row));
+                    v[u][0] = t.x; v[u][1] = t.y; v[u][2 % (2 * NC)] = t.z; v[u][3 % (2 * NC)] = t.w;
+                } else {
+                    const double2 t = __ldg(reinterpret_cast<const double2*>(row));
+                    v[u][0] = t.x; v[u][1] = t.y;
+                }
+#pragma unroll
+                for (int i = 0; i < NP; ++i) b[u][i] = __ldg(beta + (q + u) * NP + i);
             }
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                const R b = beta[q * NP + i];
+            for (int u = 0; u < 2; ++u) {
+                if (u == 1 && !two) break;
 #pragma unroll
-                for (int k = 0; k < 2 * NC; ++k) acc[i][k] += b * v[k];
+                for (int i = 0; i < NP; ++i)
+#pragma unroll
+                    for (int k = 0; k < 2 * NC; ++k) acc[i][k] += b[u][i] * v[u][k];
             }
         }
 #pragma unroll
