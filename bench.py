@@ -408,9 +408,17 @@ def run_suite(args):
     mlmd.batch_propagate(b, A[:, :2], first_handle=doms[0].handle)
     ms, _ = _timed(lambda: mlmd.batch_propagate(b, A, first_handle=doms[0].handle), reps=1)
     units = sum(sp.units_per_step for sp in specs)
+
+    def one_by_one():
+        for dd, sp in zip(doms, specs):
+            dd.propagate(sp.A, obs=True)
+    one_by_one()
+    ms_seq, _ = _timed(one_by_one, reps=1)
     lines.append({"workload": f"c3 {len(specs)} domains N~U{{24..40}}^3, N_o~U{{32..192}}, 20 steps, batched graph",
                   "ms_per_run": ms, "value": units * 20 / (ms * 1e-3), "unit": UNIT,
-                  "electrons": float(sum(sp.occ.sum() for sp in specs))})
+                  "electrons": float(sum(sp.occ.sum() for sp in specs)),
+                  "one_by_one_ms": ms_seq, "one_by_one_value": units * 20 / (ms_seq * 1e-3),
+                  "batched_speedup": ms_seq / ms})
     mlmd.batch_destroy(b)
     for dd in doms:
         dd.close()

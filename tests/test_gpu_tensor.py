@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _helpers import gpu_domain, small_spec, to_device, to_numpy
+from _helpers import gpu_domain, oracle_domain, orbitals, small_spec, to_device, to_numpy
 
 pytestmark = pytest.mark.gpu
 
@@ -85,4 +85,32 @@ def test_reorth_update_tensor_cores(mode, n, n_orb, kind):
     assert err <= 5 * TOL[mode], (mode, err)
     orth = np.max(np.abs(spec.dV * q.conj().T @ q - np.eye(n_orb)))
     assert orth <= 5 * TOL[mode], (mode, orth)
+    d.close()
+
+
+@pytest.mark.parametrize("mode,tol", [("bf16x3", 2e-5), ("bf16x2", 5e-5), ("fp16", 2e-3), ("bf16", 2e-2), ("fp32", 1e-5)])
+def test_precision_form_propagation(mode, tol):
+    """The precision form at reduced size: complex64 orbitals propagated 20
+    steps with projectors and the pulse, Cholesky re-orthonormalisation every
+    10 steps with the Gram and update GEMMs in the given split mode, against
+    the FP64 oracle; orbitals, the per-step observables (electron count,
+    energy, current) and the density and current fields after the run."""
+    spec = small_spec(precision="c64", n=(16, 16, 12), n_orb=40, steps=20, n_atoms=6)
+    d, V = gpu_domain(spec, gemm_mode=mode, ortho_every=10)
+    od = oracle_domain(spec, V)
+    psi = orbitals(spec)
+    d.set_orbitals(to_device(psi, "c64"))
+    obs = d.propagate(spec.A)
+    out = to_numpy(d.get_orbitals())
+    f = np.full(spec.n_orb, 2.0)
+    ref, robs = oracle.propagate(od, psi, spec.A, spec.dt, f, ortho_every=10)
+    assert np.max(np.abs(out - ref)) <= tol * np.abs(ref).max() * 10, (mode, np.max(np.abs(out - ref)))
+    np.testing.assert_allclose(obs[:, 0], robs[:, 0], rtol=tol)
+    np.testing.assert_allclose(obs[:, 1], robs[:, 1], rtol=tol, atol=tol * np.abs(robs[:, 0]).max())
+    scale = max(np.abs(robs[:, 2:]).max(), np.abs(robs[:, 0]).max())
+    assert np.max(np.abs(obs[:, 2:] - robs[:, 2:])) <= tol * scale
+    rho, j, J = d.density_current(spec.A[-1], device=False)
+    rr, jr, Jr = od.density_current(ref, spec.A[-1], f)
+    assert np.max(np.abs(np.asarray(rho) - rr)) <= tol * np.abs(rr).max() * 10
+    assert np.max(np.abs(np.asarray(j) - jr)) <= tol * max(np.abs(jr).max(), np.abs(rr).max()) * 10
     d.close()
