@@ -257,6 +257,37 @@ def test_batch_matches_single_domains_and_oracle():
         d.close()
 
 
+def test_batch_groups_of_plain_domains():
+    """Plain-path domains of a batch run as persistent launches per group of
+    equal FD order and projector count; a batch mixing 2nd/4th order, 4 and 8
+    projectors per atom, a domain without projectors and a TMA-path domain
+    matches the oracle domain by domain."""
+    specs = [small_spec(n=(10, 10, 10), n_orb=7, seed=1, steps=5),
+             small_spec(n=(12, 9, 11), n_orb=16, seed=2, steps=5, fd_order=2),
+             small_spec(n=(9, 10, 11), n_orb=9, seed=4, steps=5, n_proj=8, n_atoms=3),
+             small_spec(n=(10, 9, 8), n_orb=5, seed=5, steps=5, n_proj=0),
+             small_spec(n=(11, 10, 9), n_orb=12, seed=6, steps=5, n_atoms=4),
+             small_spec(n=(8, 8, 12), n_orb=3, seed=3, steps=5, n_atoms=2)]
+    from paper_2509_00966_gb300 import mlmd
+    doms, refs = [], []
+    for s in specs:
+        d, V = gpu_domain(s)
+        psi = orbitals(s)
+        d.set_orbitals(to_device(psi, s.precision))
+        doms.append(d)
+        od = oracle_domain(s, V)
+        refs.append(oracle.propagate(od, psi, s.A, s.dt, np.full(s.n_orb, 2.0)))
+    b = mlmd.batch_create([d.handle for d in doms])
+    A = np.stack([s.A for s in specs])
+    obs = mlmd.batch_propagate(b, A, first_handle=doms[0].handle)
+    for i, d in enumerate(doms):
+        assert np.max(np.abs(to_numpy(d.get_orbitals()) - refs[i][0])) <= 1e-5, i
+        _check_obs(obs[i], refs[i][1], 1e-5)
+    mlmd.batch_destroy(b)
+    for d in doms:
+        d.close()
+
+
 def test_c1_full_size_sampled_orbitals():
     """The benchmark workload (48^3 grid, 256 complex64 orbitals, 64 atoms x 4
     projectors, pulse) for 100 steps in the benchmark's launch configuration;
