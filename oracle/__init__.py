@@ -19,6 +19,8 @@ What each function follows (paper sections and equations):
                              (Sec. V.B.5, last paragraph).
 * ``overlap``/``reorth``     Eq. 5's Psi^dagger Psi product; Cholesky or
                              Loewdin re-orthonormalisation.
+* ``ks_correction``          Eq. 5: Psi(t) -= delta Psi(0) Psi^dagger(0) Psi(t),
+                             with the dV inner-product metric in Psi^dagger Psi.
 * ``loss``/``adjoint``       excited-electron count 2(N_o - sum |<psi_n(0)|psi_m(T)>|^2)
                              (Sec. V.A.8's n_exc) and its discrete adjoint.
 
@@ -324,6 +326,17 @@ def reorth(psi, dV, kind="chol"):
         return np.ascontiguousarray(sla.solve_triangular(L.conj(), psi.T, lower=True).T)
     w, U = np.linalg.eigh(S)
     return np.ascontiguousarray(psi @ ((U * (1.0 / np.sqrt(w))) @ U.conj().T))
+
+
+def ks_correction(psi_t, psi_0, delta, dV):
+    """Eq. 5, the nonlocal correction in the space of the Kohn-Sham orbitals:
+    Psi(t) <- Psi(t) - delta Psi(0) C with C = dV Psi(0)^H Psi(t) (the
+    overlap in the grid's inner product, so delta is dimensionless).
+    Two matrix products, as the equation is written."""
+    psi_t = _c128(psi_t)
+    psi_0 = _c128(psi_0)
+    C = overlap(psi_0, psi_t, dV)
+    return np.ascontiguousarray(psi_t - complex(delta) * (psi_0 @ C))
 
 
 def loss(psi_ref, psi_T, dV):

@@ -47,3 +47,30 @@ def test_pins_catch_planted_mistake(name, old, new, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
+KS_MUTANTS = [
+    ("overlap transposed", "psi_0 @ C", "psi_0 @ C.T"),
+    ("overlap conjugated", "psi_0 @ C", "psi_0 @ C.conj()"),
+    ("sign of delta", "psi_t - complex(delta)", "psi_t + complex(delta)"),
+    ("missing dV", "C = overlap(psi_0, psi_t, dV)", "C = overlap(psi_0, psi_t, 1.0)"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", KS_MUTANTS, ids=[m[0] for m in KS_MUTANTS])
+def test_ks_pin_catches_planted_mistake(name, old, new, monkeypatch):
+    """Eq. 5's oracle function with one planted mistake (rebuilt from the
+    oracle's own source text) must fail the closed-form pin."""
+    import inspect
+    import textwrap
+    sys.path.insert(0, ROOT)
+    import oracle
+    src = textwrap.dedent(inspect.getsource(oracle.ks_correction))
+    assert src.count(old) == 1, name
+    ns = {"np": __import__("numpy"), "overlap": oracle.overlap, "_c128": oracle._c128}
+    exec(src.replace(old, new), ns)
+    monkeypatch.setattr(oracle, "ks_correction", ns["ks_correction"])
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import test_oracle_pins
+    with pytest.raises(AssertionError):
+        test_oracle_pins.test_ks_correction_closed_forms()

@@ -406,3 +406,28 @@ def test_adjoint_dot_product_identity():
     lhs = np.vdot(dom.taylor4_adjoint(y, A, 0.03), x)
     rhs = np.vdot(y, dom.taylor4(x, A, 0.03))
     assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+def test_ks_correction_closed_forms():
+    """Eq. 5 pinned without retyping it: with Psi(0) orthonormal in the dV
+    metric and Psi(t) = Psi(0) A + Q B, Q orthogonal to span Psi(0), the
+    correction must give (1 - delta) Psi(0) A + Q B for general complex A, B
+    (a transposed or conjugated overlap, a missing dV or a wrong sign of
+    delta all break it); delta = 0 is the identity."""
+    rng = np.random.default_rng(11)
+    ng, no, dV = 300, 7, 0.064
+    # an orthonormal basis of 12 columns: the first 7 span Psi(0), 5 span Q
+    Z = rng.standard_normal((ng, 12)) + 1j * rng.standard_normal((ng, 12))
+    Qf, _ = np.linalg.qr(Z)
+    basis = Qf / np.sqrt(dV)
+    psi0, Q = basis[:, :no], basis[:, no:]
+    A = rng.standard_normal((no, no)) + 1j * rng.standard_normal((no, no))
+    B = rng.standard_normal((5, no)) + 1j * rng.standard_normal((5, no))
+    psit = psi0 @ A + Q @ B
+    delta = 0.03 - 0.017j
+    out = oracle.ks_correction(psit, psi0, delta, dV)
+    np.testing.assert_allclose(out, (1 - delta) * (psi0 @ A) + Q @ B, rtol=0, atol=1e-12 * np.abs(psit).max())
+    np.testing.assert_allclose(oracle.ks_correction(psit, psi0, 0.0, dV), psit, rtol=0, atol=0)
+    # Psi(t) = Psi(0): every orbital scales by 1 - delta
+    np.testing.assert_allclose(oracle.ks_correction(psi0, psi0, delta, dV), (1 - delta) * psi0, rtol=0,
+                               atol=1e-12 * np.abs(psi0).max())
