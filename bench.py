@@ -47,6 +47,8 @@ def _args():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
+    p.add_argument("--ks", nargs=3, metavar=("N", "N_ORB", "MODE"),
+                   help="time the Eq. 5 KS-space nonlocal correction on an N^3 x N_ORB complex64 domain in gemm MODE")
     p.add_argument("--reorth", nargs=3, metavar=("N", "N_ORB", "MODE"),
                    help="time Cholesky re-orthonormalisations of an N^3 x N_ORB complex64 domain in gemm MODE")
     p.add_argument("--gram", nargs=3, metavar=("N", "N_ORB", "MODE"),
@@ -469,6 +471,35 @@ def run_gram(args):
     d.close()
 
 
+def run_ks(args):
+    """Time mlmd_ks_correction (Eq. 5: C = dV Psi(0)^H Psi(t), then
+    Psi(t) - delta Psi(0) C) on an N^3 x N_ORB complex64 domain; reports ms
+    per call and the tensor FLOP/s of the two real-embedded GEMMs
+    (2 (2 ld)^2 N_g each, times the split mode's products)."""
+    import torch
+    from paper_2509_00966_gb300 import build, mlmd
+    build.build()
+    n, no, mode = int(args.ks[0]), int(args.ks[1]), args.ks[2]
+    h = 0.35
+    d = mlmd.Domain((n, n, n), h, no, 4, "c64", gemm_mode=mode)
+    d.set_orbitals(_device_orbitals(n ** 3, no, h ** 3, 2, torch.complex64))
+    d.ks_correction(0.01 - 0.005j)
+    ms, _ = _timed(lambda: d.ks_correction(0.01 - 0.005j), reps=3)
+    ld = (no + 7) // 8 * 8
+    nprod = {"bf16": 1, "bf16x2": 3, "bf16x3": 6, "fp16": 1, "fp32": 1}[mode]
+    flops = 2 * 2.0 * (2 * ld) ** 2 * n ** 3 * nprod
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    print(json.dumps({"kernel": "ks_correction (Eq. 5)", "grid": n, "n_orb": no, "mode": mode, "ms": ms,
+                      "tensor_tflops": flops / (ms * 1e-3) / 1e12, "peak_bf16_tflops": peak,
+                      "frac": flops / (ms * 1e-3) / 1e12 / peak}), flush=True)
+    d.close()
+
+
 def run_reorth(args):
     """Time mlmd_reorthonormalize (FP64 Cholesky on the device, Gram and
     update GEMMs in the given gemm mode) on an N^3 x N_ORB complex64 domain
@@ -496,6 +527,8 @@ def main():
         run_gram(args)
     elif args.reorth:
         run_reorth(args)
+    elif args.ks:
+        run_ks(args)
     elif args.suite:
         run_suite(args)
     else:

@@ -188,6 +188,16 @@ MLMD_API mlmd_status mlmd_reorthonormalize(mlmd_domain_t dom, int32_t kind);
  * (the per-domain n_exc of Sec. V.A.8). */
 MLMD_API mlmd_status mlmd_excitation(mlmd_domain_t dom, double* n_exc);
 
+/* KS-space nonlocal correction of Eq. 5 (Sec. V.B.5) applied once to the
+ * current orbitals: Psi(t) <- Psi(t) - delta Psi(0) C with C = dV Psi(0)^H
+ * Psi(t), the overlap with the reference orbitals from mlmd_set_orbitals in
+ * the grid's inner product (so delta is dimensionless).  delta: host double
+ * [2] = (Re, Im).  Both products run as GEMMs in the domain's gemm_mode
+ * (tcgen05 split operands for complex64 and non-FP32 modes).  Returns
+ * MLMD_ERR_STATE without reference orbitals, MLMD_ERR_INVALID for a null or
+ * non-finite delta. */
+MLMD_API mlmd_status mlmd_ks_correction(mlmd_domain_t dom, const double* delta);
+
 /* Gradients of L = n_exc(Psi(T)) after n_steps full-scheme steps from the
  * current orbitals, by the discrete adjoint of the Taylor map.  The forward
  * pass keeps every ckpt_every-th state and recomputes the others inside each

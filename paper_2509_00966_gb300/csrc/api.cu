@@ -609,6 +609,24 @@ mlmd_status mlmd_excitation(mlmd_domain_t d, double* n_exc) {
     });
 }
 
+mlmd_status mlmd_ks_correction(mlmd_domain_t d, const double* delta) {
+    return guarded(d, [&] {
+        MLMD_REQUIRE(delta != nullptr && std::isfinite(delta[0]) && std::isfinite(delta[1]), MLMD_ERR_INVALID,
+                     "delta must be two finite numbers");
+        MLMD_REQUIRE(d->psi0_valid, MLMD_ERR_STATE, "no reference orbitals (call mlmd_set_orbitals)");
+        const int n = d->desc.n_orb;
+        double* C = ensure_dense(*d, (size_t)n * n * 2);
+        // C = dV Psi(0)^H Psi(t), then C <- -delta C, then Psi(t) + Psi(0) C
+        launch_overlap(*d, d->psi0, d->psi, d->desc.h * d->desc.h * d->desc.h, C);
+        launch_scale_complex(*d, C, (int64_t)n * n, -delta[0], -delta[1]);
+        if (!launch_gemm_add_tc(*d, d->psi0, C, d->psi, d->wa)) launch_update(*d, d->psi0, C, d->wa, d->psi);
+        std::swap(d->psi, d->wa);
+        d->pa_psi = false;
+        MLMD_CUDA(cudaStreamSynchronize(d->stream));
+        check_err_flag(*d);
+    });
+}
+
 mlmd_status mlmd_profile_enable(mlmd_domain_t d, int32_t enable) {
     return guarded(d, [&] {
         MLMD_CUDA(cudaStreamSynchronize(d->stream));

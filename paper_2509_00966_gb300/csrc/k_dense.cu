@@ -85,7 +85,7 @@ __global__ void k_overlap_reduce(const double* __restrict__ part, int nsplit, in
 // points ty + 16 a (a < 4) and the orbitals tx + 16 b (b < 2) of the tile.
 template <typename R>
 __global__ void __launch_bounds__(256) k_update(const R* __restrict__ X, const double* __restrict__ M, int64_t ng,
-                                                int ld, int n_orb, R* __restrict__ Y) {
+                                                int ld, int n_orb, const R* __restrict__ Z, R* __restrict__ Y) {
     __shared__ R xs[64][33][2];
     __shared__ R ms[32][33][2];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -134,8 +134,9 @@ __global__ void __launch_bounds__(256) k_update(const R* __restrict__ X, const d
             const int64_t g = gb + ty + 16 * a;
             const int m = m0 + tx + 16 * b;
             if (g < ng && m < ld) {
-                Y[(g * ld + m) * 2] = m < n_orb ? acc[a][b][0] : (R)0;
-                Y[(g * ld + m) * 2 + 1] = m < n_orb ? acc[a][b][1] : (R)0;
+                const R zr = Z ? Z[(g * ld + m) * 2] : (R)0, zi = Z ? Z[(g * ld + m) * 2 + 1] : (R)0;
+                Y[(g * ld + m) * 2] = m < n_orb ? zr + acc[a][b][0] : (R)0;
+                Y[(g * ld + m) * 2 + 1] = m < n_orb ? zi + acc[a][b][1] : (R)0;
             }
         }
 }
@@ -479,11 +480,29 @@ void launch_overlap(Domain& d, const void* X, const void* Y, double scale, doubl
     d.mem.put(part);
 }
 
-void launch_update(Domain& d, const void* X, const double* M, void* Y) {
+void launch_update(Domain& d, const void* X, const double* M, void* Y, const void* Z) {
     const int no = d.desc.n_orb;
     dim3 grid((d.ld + 31) / 32, (unsigned)((d.ng + 63) / 64));
-    if (d.c64()) k_update<float><<<grid, 256, 0, d.stream>>>((const float*)X, M, d.ng, d.ld, no, (float*)Y);
-    else k_update<double><<<grid, 256, 0, d.stream>>>((const double*)X, M, d.ng, d.ld, no, (double*)Y);
+    if (d.c64())
+        k_update<float><<<grid, 256, 0, d.stream>>>((const float*)X, M, d.ng, d.ld, no, (const float*)Z, (float*)Y);
+    else
+        k_update<double><<<grid, 256, 0, d.stream>>>((const double*)X, M, d.ng, d.ld, no, (const double*)Z,
+                                                     (double*)Y);
+    d.launches++;
+    MLMD_CUDA(cudaGetLastError());
+}
+
+// M <- s M for a complex FP64 [n][n] matrix and complex s.
+__global__ void k_scale_complex(double* __restrict__ M, int64_t nn, double sr, double si) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+        const double a = M[2 * e], b = M[2 * e + 1];
+        M[2 * e] = sr * a - si * b;
+        M[2 * e + 1] = sr * b + si * a;
+    }
+}
+
+void launch_scale_complex(Domain& d, double* M, int64_t nn, double sr, double si) {
+    k_scale_complex<<<(int)std::min<int64_t>((nn + 255) / 256, 1024), 256, 0, d.stream>>>(M, nn, sr, si);
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
 }

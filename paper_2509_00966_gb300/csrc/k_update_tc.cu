@@ -1,16 +1,17 @@
-// Orbital update Y = X M on the tcgen05 tensor cores (Sec. V.B.7, the
-// re-orthonormalisation Psi <- Psi L^{-H} of Sec. VI.C), written as
+// Orbital updates Y = Z + X Mc on the tcgen05 tensor cores (Sec. V.B.7):
+// the re-orthonormalisation Psi <- Psi L^{-H} of Sec. VI.C, written as
 // Y = X + X (M - I) so that the split-precision error scales with |M - I|,
-// which is small when the orbitals were nearly orthonormal already.
+// which is small when the orbitals were nearly orthonormal already; and the
+// KS-space nonlocal correction of Eq. 5, Psi(t) + Psi(0) (-delta C).
 //
 // For complex64 X ([N_g][ld] interleaved) the complex product is one real
 // GEMM on the real view Xr ([N_g][2 ld]):  Yr = Xr + Xr R  with the real
 // 2ld x 2ld embedding R of M - I:
 //     R[2a][2b] = R[2a+1][2b+1] = Re(M - I)[a][b],
 //     R[2a][2b+1] = Im M[a][b],   R[2a+1][2b] = -Im M[a][b].
-// The MMA's M dimension is the grid point (128 points per tile), N the output
-// real column (128 per tile) and K the input real column.  A = Xr is K-major
-// as stored; B is R^T, built K-major from M.  Both are split once into 16-bit
+// (R embeds Mc the same way.)  The MMA's M dimension is the grid point (128
+// points per tile), N the output real column (128 per tile) and K the input
+// real column.  A = Xr is K-major as stored; B is R^T, built K-major from M.  Both are split once into 16-bit
 // parts and stored as 16 KiB canonical tile images (the layout of the Gram
 // kernel); the GEMM kernel streams them with bulk copies through a ring of
 // shared-memory stages, accumulates all split products in FP32 in tensor
@@ -71,14 +72,14 @@ __global__ void __launch_bounds__(256) k_split_rows(const float* __restrict__ X,
     }
 }
 
-// Largest |entry| of M - I (as FP32 bits; non-negative floats order like
-// their bit patterns), for the FP16 scale of R.
-__global__ void k_update_maxabs(const double* __restrict__ M, int n, unsigned int* __restrict__ out) {
+// Largest |entry| of M - I (sub_id) or M (as FP32 bits; non-negative floats
+// order like their bit patterns), for the FP16 scale of R.
+__global__ void k_update_maxabs(const double* __restrict__ M, int n, int sub_id, unsigned int* __restrict__ out) {
     float m = 0.f;
     const int64_t nn = (int64_t)n * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
         const int a = (int)(e / n), b = (int)(e % n);
-        const double re = M[e * 2] - (a == b ? 1.0 : 0.0), im = M[e * 2 + 1];
+        const double re = M[e * 2] - (sub_id && a == b ? 1.0 : 0.0), im = M[e * 2 + 1];
         m = fmaxf(m, (float)fmax(fabs(re), fabs(im)));
     }
 #pragma unroll
@@ -98,7 +99,7 @@ __device__ __forceinline__ float r_scale(const unsigned int* maxbits) {
 // Split pass for B: tile images of R^T, parts[p][jt][kt], 128 output real
 // columns j (rows of the tile) x 64 input real columns k (K).  Block (kt, jt).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_split_embed(const double* __restrict__ M, int n, int njt, int nkt,
+__global__ void __launch_bounds__(256) k_split_embed(const double* __restrict__ M, int n, int sub_id, int njt, int nkt,
                                                      const unsigned int* __restrict__ maxbits,
                                                      unsigned char* __restrict__ parts) {
     constexpr int NPART = Split<MODE>::NPART;
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256) k_split_embed(const double* __restrict__ 
             const int k = kt * BK + kg * 8 + i, a = k >> 1, s = k & 1;
             float v = 0.f;
             if (a < n && b < n) {
-                const double re = M[((int64_t)a * n + b) * 2] - (a == b ? 1.0 : 0.0);
+                const double re = M[((int64_t)a * n + b) * 2] - (sub_id && a == b ? 1.0 : 0.0);
                 const double im = M[((int64_t)a * n + b) * 2 + 1];
                 v = (float)(s == t ? re : (s == 0 ? im : -im));
             }
@@ -139,12 +140,12 @@ __global__ void __launch_bounds__(256) k_split_embed(const double* __restrict__ 
 // ring of STAGES shared-memory buffers, thread 32 issues the MMAs (all split
 // products of each K-step into one FP32 accumulator) and frees each buffer
 // with a commit; then the four warps read their 32 rows of the accumulator
-// and write Y = X + unscale * acc.  Every wait is bounded; on a timeout the
+// and write Y = Z + unscale * acc.  Every wait is bounded; on a timeout the
 // kernel raises *err, lets copies in flight land and frees tensor memory.
 template <int MODE>
 __global__ void __launch_bounds__(128, 1)
     k_update_tc(const unsigned char* __restrict__ pa, const unsigned char* __restrict__ pb, int ngt, int njt, int nkt,
-                const float* __restrict__ X, float* __restrict__ Y, int64_t ng, int ncols, float xunscale,
+                const float* __restrict__ Z, float* __restrict__ Y, int64_t ng, int ncols, float xunscale,
                 const unsigned int* __restrict__ maxbits, int* __restrict__ err) {
     constexpr int NPART = Split<MODE>::NPART, NPROD = Split<MODE>::NPROD, STAGES = Stages<MODE>::value;
     constexpr uint32_t STAGE_BYTES = 2 * NPART * kTileBytes;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(128, 1)
                 for (int q = 0; q < 8; ++q) {
                     const int j = j0 + 4 * q;
                     if (j < ncols) {
-                        const float4 x = *reinterpret_cast<const float4*>(X + g * ncols + j);
+                        const float4 x = *reinterpret_cast<const float4*>(Z + g * ncols + j);
                         float4 y;
                         y.x = x.x + unscale * v[4 * q];
                         y.y = x.y + unscale * v[4 * q + 1];
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 template <int MODE>
-void update_mode(Domain& d, const float* X, const double* M, float* Y) {
+void update_mode(Domain& d, const float* X, const double* M, int sub_id, const float* Z, float* Y) {
     constexpr int NPART = Split<MODE>::NPART, STAGES = Stages<MODE>::value;
     const int n = d.desc.n_orb, ncols = 2 * d.ld;
     const int ngt = (int)((d.ng + BM - 1) / BM);
@@ -281,15 +282,15 @@ void update_mode(Domain& d, const float* X, const double* M, float* Y) {
     MLMD_CUDA(cudaMemsetAsync(maxbits, 0, sizeof(unsigned int), d.stream));
     if (MODE == MLMD_GEMM_FP16) {
         const int64_t nn = (int64_t)n * n;
-        k_update_maxabs<<<(int)std::min<int64_t>((nn + 255) / 256, 1024), 256, 0, d.stream>>>(M, n, maxbits);
+        k_update_maxabs<<<(int)std::min<int64_t>((nn + 255) / 256, 1024), 256, 0, d.stream>>>(M, n, sub_id, maxbits);
         d.launches++;
     }
     k_split_rows<MODE><<<dim3(nkt, ngt), 256, 0, d.stream>>>(X, d.ng, ncols, ngt, nkt, fx, pa);
-    k_split_embed<MODE><<<dim3(nkt, njt), 256, 0, d.stream>>>(M, n, njt, nkt, maxbits, pb);
+    k_split_embed<MODE><<<dim3(nkt, njt), 256, 0, d.stream>>>(M, n, sub_id, njt, nkt, maxbits, pb);
     d.launches += 2;
     constexpr uint32_t smem = STAGES * 2 * NPART * kTileBytes + 1024;
     ensure_dynamic_smem(reinterpret_cast<const void*>(k_update_tc<MODE>), smem);
-    k_update_tc<MODE><<<dim3(njt, ngt), 128, smem, d.stream>>>(pa, pb, ngt, njt, nkt, X, Y, d.ng, ncols, xunscale,
+    k_update_tc<MODE><<<dim3(njt, ngt), 128, smem, d.stream>>>(pa, pb, ngt, njt, nkt, Z, Y, d.ng, ncols, xunscale,
                                                                maxbits, d.err_flag);
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
@@ -300,18 +301,29 @@ void update_mode(Domain& d, const float* X, const double* M, float* Y) {
 
 }  // namespace
 
-bool launch_update_tc(Domain& d, const void* X, const double* M, void* Y) {
+namespace {
+
+bool gemm_tc(Domain& d, const void* X, const double* M, int sub_id, const void* Z, void* Y) {
     const int mode = d.desc.gemm_mode;
     if (!d.c64() || mode == MLMD_GEMM_FP32) return false;
     const float* Xf = static_cast<const float*>(X);
+    const float* Zf = static_cast<const float*>(Z);
     float* Yf = static_cast<float*>(Y);
     switch (mode) {
-        case MLMD_GEMM_BF16: update_mode<MLMD_GEMM_BF16>(d, Xf, M, Yf); break;
-        case MLMD_GEMM_BF16X2: update_mode<MLMD_GEMM_BF16X2>(d, Xf, M, Yf); break;
-        case MLMD_GEMM_BF16X3: update_mode<MLMD_GEMM_BF16X3>(d, Xf, M, Yf); break;
-        default: update_mode<MLMD_GEMM_FP16>(d, Xf, M, Yf); break;
+        case MLMD_GEMM_BF16: update_mode<MLMD_GEMM_BF16>(d, Xf, M, sub_id, Zf, Yf); break;
+        case MLMD_GEMM_BF16X2: update_mode<MLMD_GEMM_BF16X2>(d, Xf, M, sub_id, Zf, Yf); break;
+        case MLMD_GEMM_BF16X3: update_mode<MLMD_GEMM_BF16X3>(d, Xf, M, sub_id, Zf, Yf); break;
+        default: update_mode<MLMD_GEMM_FP16>(d, Xf, M, sub_id, Zf, Yf); break;
     }
     return true;
+}
+
+}  // namespace
+
+bool launch_update_tc(Domain& d, const void* X, const double* M, void* Y) { return gemm_tc(d, X, M, 1, X, Y); }
+
+bool launch_gemm_add_tc(Domain& d, const void* X, const double* Mc, const void* Z, void* Y) {
+    return gemm_tc(d, X, Mc, 0, Z, Y);
 }
 
 }  // namespace mlmd

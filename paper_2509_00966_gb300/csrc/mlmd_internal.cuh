@@ -237,10 +237,16 @@ void launch_overlap(Domain& d, const void* X, const void* Y, double scale, doubl
 // complex64 domains whose gemm_mode is not FP32 (returns false otherwise).
 bool launch_overlap_tc(Domain& d, const void* X, const void* Y, double scale, double* S);
 // Y[g][m] = sum_n X[g][n] M[n][m] (M complex double [n_orb][n_orb], device)
-void launch_update(Domain& d, const void* X, const double* M, void* Y);
+// Y = Z + X M (Z = null: Y = X M), SIMT, FP32 or FP64 accumulation per the domain.
+void launch_update(Domain& d, const void* X, const double* M, void* Y, const void* Z = nullptr);
+// M <- (sr + i si) M for a complex FP64 matrix of nn entries.
+void launch_scale_complex(Domain& d, double* M, int64_t nn, double sr, double si);
 // Y = X M on the tensor cores in the domain's split mode (c64, non-FP32 GEMM
 // modes); false if the domain does not use them.
 bool launch_update_tc(Domain& d, const void* X, const double* M, void* Y);
+// Y = Z + X Mc on the tensor cores in the domain's split mode (Mc complex
+// FP64 [n_orb][n_orb]); false if the domain does not use them.
+bool launch_gemm_add_tc(Domain& d, const void* X, const double* Mc, const void* Z, void* Y);
 // In place: S -> lower Cholesky factor L (S = L L^H); returns false if S is
 // not positive definite.  Then Minv = L^{-H} (upper).
 void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info);

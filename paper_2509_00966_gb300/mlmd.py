@@ -65,6 +65,7 @@ _SIGS = {
     "mlmd_overlap": (ctypes.c_int, [_P, _P]),
     "mlmd_reorthonormalize": (ctypes.c_int, [_P, ctypes.c_int32]),
     "mlmd_excitation": (ctypes.c_int, [_P, _P]),
+    "mlmd_ks_correction": (ctypes.c_int, [_P, _P]),
     "mlmd_propagate_adjoint": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32]),
     "mlmd_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.POINTER(_P)]),
     "mlmd_batch_destroy": (ctypes.c_int, [_P]),
@@ -238,6 +239,12 @@ def excitation(h):
     return v.value
 
 
+def ks_correction(h, delta):
+    """Eq. 5 once: Psi(t) -= delta Psi(0) (dV Psi(0)^H Psi(t)); delta complex."""
+    dl = np.array([complex(delta).real, complex(delta).imag], np.float64)
+    _check(lib().mlmd_ks_correction(h, ctypes.c_void_p(dl.ctypes.data)), h)
+
+
 def propagate_adjoint(h, A, ckpt_every, n_grid, dL_dV=None):
     A = _f64(A).reshape(-1, 3)
     loss = ctypes.c_double()
@@ -399,6 +406,9 @@ class Domain:
 
     def excitation(self):
         return excitation(self.handle)
+
+    def ks_correction(self, delta):
+        ks_correction(self.handle, delta)
 
     def propagate_adjoint(self, A, ckpt_every, dL_dV=None):
         return propagate_adjoint(self.handle, A, ckpt_every, self.n_grid, dL_dV)

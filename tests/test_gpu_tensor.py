@@ -114,3 +114,40 @@ def test_precision_form_propagation(mode, tol):
     assert np.max(np.abs(np.asarray(rho) - rr)) <= tol * np.abs(rr).max() * 10
     assert np.max(np.abs(np.asarray(j) - jr)) <= tol * max(np.abs(jr).max(), np.abs(rr).max()) * 10
     d.close()
+
+
+@pytest.mark.parametrize("precision,mode,tol", [("c128", "fp32", 1e-12), ("c64", "fp32", 2e-6), ("c64", "bf16x3", 2e-5),
+                                                ("c64", "bf16x2", 1e-4), ("c64", "fp16", 2e-3), ("c64", "bf16", 1e-2)])
+@pytest.mark.parametrize("n,n_orb", [((12, 10, 14), 37), ((16, 16, 16), 150)])
+def test_ks_correction(precision, mode, tol, n, n_orb):
+    """Eq. 5 through mlmd_ks_correction (overlap with Psi(0) and the update,
+    both GEMMs in the domain's mode) against the oracle on the same Psi(t):
+    the error of the correction term scales with |delta| and the mode."""
+    from paper_2509_00966_gb300 import mlmd
+    spec = small_spec(precision=precision, n=n, n_orb=n_orb, steps=3)
+    d, V = gpu_domain(spec, gemm_mode=mode)
+    psi0 = orbitals(spec)
+    d.set_orbitals(to_device(psi0, precision))
+    d.propagate(spec.A)                          # Psi(t) != Psi(0)
+    psit = to_numpy(d.get_orbitals())
+    p0 = to_numpy(to_device(psi0, precision))    # Psi(0) as the domain holds it
+    delta = 0.05 - 0.02j
+    d.ks_correction(delta)
+    out = to_numpy(d.get_orbitals())
+    ref = oracle.ks_correction(psit, p0, delta, spec.dV)
+    scale = np.abs(ref).max()
+    bound = tol * abs(delta) * scale * 10 + (1e-12 if precision == "c128" else 2e-7) * scale
+    assert np.max(np.abs(out - ref)) <= bound, (mode, np.max(np.abs(out - ref)) / scale)
+    # delta = 0 leaves the orbitals exactly as they are
+    d.ks_correction(0.0)
+    assert np.array_equal(to_numpy(d.get_orbitals()), out)
+    d.close()
+
+
+def test_ks_correction_needs_reference_orbitals():
+    from paper_2509_00966_gb300 import mlmd
+    spec = small_spec(precision="c64", steps=1)
+    d, V = gpu_domain(spec, gemm_mode="bf16x3")
+    with pytest.raises(mlmd.MLMDError):
+        d.ks_correction(0.1)
+    d.close()
