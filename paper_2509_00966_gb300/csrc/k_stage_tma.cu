@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     unsigned char* sE = reinterpret_cast<unsigned char*>(sP + N.maxs * NPV * VP);   // [NSLOT][scap] entry blocks
     __shared__ __align__(8) uint64_t bars[NSLOT];
     __shared__ __align__(8) uint64_t pbars[PSL];
+    __shared__ int64_t soff[17];                    // entry-block offsets of the column's planes (zc <= 16)
     __shared__ R sA[4];
     __shared__ int abort_sh;
 
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     if (tid == 3) sA[3] = (R)(0.5 * (Ak[0] * Ak[0] + Ak[1] * Ak[1] + Ak[2] * Ak[2]));
     int cs = 0, na = 0;
     if (NP > 0) {
+        if (tid <= nzc) soff[tid] = N.sblk_off[(int64_t)col * G.zc + tid];
         cs = N.col_start[col];
         na = N.col_start[col + 1] - cs;
         for (int idx = tid; idx < na * NPV * VP; idx += NT) {
@@ -329,9 +331,8 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         uint32_t eb = 0;
         int64_t eo = 0;
         if (NP > 0 && j >= 0 && j < nzc) {
-            const int64_t blk = (int64_t)col * G.zc + j;
-            eo = N.sblk_off[blk];
-            eb = (uint32_t)(N.sblk_off[blk + 1] - eo);
+            eo = soff[j];
+            eb = (uint32_t)(soff[j + 1] - eo);
         }
         mbar_expect_tx(b, Slot<VP>::BYTES + eb);
         if (eb) bulk_g2s(sE + (size_t)s * N.scap, N.sblk + eo, eb, b);
