@@ -23,6 +23,9 @@ What each function follows (paper sections and equations):
                              with the dV inner-product metric in Psi^dagger Psi.
 * ``loss``/``adjoint``       excited-electron count 2(N_o - sum |<psi_n(0)|psi_m(T)>|^2)
                              (Sec. V.A.8's n_exc) and its discrete adjoint.
+* ``occupations``            shadow-dynamics occupations f_s of the reference
+                             orbitals and n_exc computed from them (Sec. V.A.3,
+                             V.A.4 and V.A.8).
 
 Parity pins: see ``tests/test_oracle_pins.py``; every function above is pinned
 there against a dense eigendecomposition, closed forms, or brute force.
@@ -343,6 +346,20 @@ def loss(psi_ref, psi_T, dV):
     """n_exc = 2 (N_o - sum_{n,m} |<psi_n(0)|psi_m(T)>|^2)."""
     C = overlap(psi_ref, psi_T, dV)
     return 2.0 * (psi_ref.shape[1] - float(np.sum(np.abs(C) ** 2)))
+
+
+def occupations(psi_ref, psi_t, f, dV):
+    """Occupation numbers handed from LFD back to QXMD (Sec. V.A.3-4) and the
+    excited-electron count computed from them (Sec. V.A.8).  The reference
+    orbitals psi_s(0) are the adiabatic states; the propagated orbitals
+    psi_n(t) carry the occupations f_n.  The occupation of reference state s
+    at time t is f_s(t) = sum_n f_n |<psi_s(0)|psi_n(t)>|^2, and
+    n_exc = sum_n f_n - sum_s f_s(t), the electrons that have left the span
+    of the reference orbitals.  Returns (f_s(t) [N_o], n_exc)."""
+    C = overlap(psi_ref, psi_t, dV)          # C[s][n] = <psi_s(0)|psi_n(t)>
+    f = np.asarray(f, np.float64)
+    f_s = (np.abs(C) ** 2) @ f
+    return f_s, float(np.sum(f) - np.sum(f_s))
 
 
 def propagate(dom: Domain, psi, A, dt, f, scheme="full", ortho_every=0, ortho_kind="chol", step0=0):

@@ -74,3 +74,30 @@ def test_ks_pin_catches_planted_mistake(name, old, new, monkeypatch):
     import test_oracle_pins
     with pytest.raises(AssertionError):
         test_oracle_pins.test_ks_correction_closed_forms()
+
+
+OCC_MUTANTS = [
+    ("overlap transposed", "(np.abs(C) ** 2) @ f", "(np.abs(C) ** 2).T @ f"),
+    ("reference and propagated swapped", "C = overlap(psi_ref, psi_t, dV)", "C = overlap(psi_t, psi_ref, dV)"),
+    ("missing dV", "C = overlap(psi_ref, psi_t, dV)", "C = overlap(psi_ref, psi_t, 1.0)"),
+    ("sign of n_exc", "np.sum(f) - np.sum(f_s)", "np.sum(f_s) - np.sum(f)"),
+    ("amplitudes instead of probabilities", "(np.abs(C) ** 2) @ f", "np.abs(C) @ f"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", OCC_MUTANTS, ids=[m[0] for m in OCC_MUTANTS])
+def test_occupations_pin_catches_planted_mistake(name, old, new, monkeypatch):
+    """The occupation function with one planted mistake must fail its pin."""
+    import inspect
+    import textwrap
+    sys.path.insert(0, ROOT)
+    import oracle
+    src = textwrap.dedent(inspect.getsource(oracle.occupations))
+    assert src.count(old) == 1, name
+    ns = {"np": __import__("numpy"), "overlap": oracle.overlap}
+    exec(src.replace(old, new), ns)
+    monkeypatch.setattr(oracle, "occupations", ns["occupations"])
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import test_oracle_pins
+    with pytest.raises(AssertionError):
+        test_oracle_pins.test_occupations_closed_forms()

@@ -431,3 +431,42 @@ def test_ks_correction_closed_forms():
     # Psi(t) = Psi(0): every orbital scales by 1 - delta
     np.testing.assert_allclose(oracle.ks_correction(psi0, psi0, delta, dV), (1 - delta) * psi0, rtol=0,
                                atol=1e-12 * np.abs(psi0).max())
+
+
+def test_occupations_closed_forms():
+    """Shadow-dynamics occupations pinned by construction: with Psi(0)
+    orthonormal in the dV metric, Psi(t) = cos(t) Psi(0) U + sin(t) Q W (U, W
+    unitary, Q orthonormal and orthogonal to span Psi(0)) gives
+    f_s(t) = cos^2(t) sum_n f_n |U_sn|^2 and n_exc = sin^2(t) sum_n f_n, for
+    unequal occupations and a non-symmetric U (so a transposed overlap, a
+    missing dV or a wrong sign of n_exc break it).  Diagonal phases keep
+    every occupation; a state orthogonal to the reference has none."""
+    rng = np.random.default_rng(12)
+    ng, no, dV = 320, 6, 0.064
+    Z = rng.standard_normal((ng, 2 * no)) + 1j * rng.standard_normal((ng, 2 * no))
+    Qf, _ = np.linalg.qr(Z)
+    basis = Qf / np.sqrt(dV)
+    psi0, Q = basis[:, :no], basis[:, no:]
+
+    def unitary():
+        M = rng.standard_normal((no, no)) + 1j * rng.standard_normal((no, no))
+        q, r = np.linalg.qr(M)
+        return q * (np.diag(r) / np.abs(np.diag(r)))
+
+    U, W = unitary(), unitary()
+    assert np.abs(np.abs(U) - np.abs(U).T).max() > 0.1
+    f = rng.uniform(0.2, 2.0, no)
+    t = 0.37
+    psit = np.cos(t) * (psi0 @ U) + np.sin(t) * (Q @ W)
+    f_s, n_exc = oracle.occupations(psi0, psit, f, dV)
+    np.testing.assert_allclose(f_s, np.cos(t) ** 2 * (np.abs(U) ** 2 @ f), rtol=1e-12, atol=1e-13)
+    assert abs(n_exc - np.sin(t) ** 2 * f.sum()) < 1e-12 * f.sum()
+    phases = np.exp(1j * rng.uniform(0, 2 * np.pi, no))
+    f_s, n_exc = oracle.occupations(psi0, psi0 * phases, f, dV)
+    np.testing.assert_allclose(f_s, f, rtol=1e-12)
+    assert abs(n_exc) < 1e-12 * f.sum()
+    f_s, n_exc = oracle.occupations(psi0, Q @ W, f, dV)
+    assert np.abs(f_s).max() < 1e-12 and abs(n_exc - f.sum()) < 1e-12 * f.sum()
+    # with f_n = 2 the count is the loss of Sec. V.A.8 (2 (N_o - sum |C|^2))
+    _, n2 = oracle.occupations(psi0, psit, np.full(no, 2.0), dV)
+    assert abs(n2 - oracle.loss(psi0, psit, dV)) < 1e-12 * no
