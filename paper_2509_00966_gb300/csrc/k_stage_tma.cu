@@ -293,11 +293,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     // psi_mode 0: out = gamma h w; 1: psi is w itself (its centre tile is in
     // the ring already); 2: psi's centre tile comes with each plane
     const bool has_psi = psi_mode != 0;
-    // complex64 launches without observables take the packed path: h w as
-    // sum_n c_n w_n with the complex coefficient c_n = k_n - i a_n of each
-    // stencil neighbour (k from the Laplacian, a = A . gradient weight),
-    // evaluated as f32x2 multiply-adds on (re, im) pairs
-    constexpr bool FAST = std::is_same<R, float>::value && !OBS;
+    // complex64 launches take the packed path: h w as sum_n c_n w_n with the
+    // complex coefficient c_n = k_n - i a_n of each stencil neighbour (k from
+    // the Laplacian, a = A . gradient weight), evaluated as f32x2
+    // multiply-adds on (re, im) pairs; with observables the gradient is kept
+    // per axis for the current and the sums run on packed pairs too
+    constexpr bool FAST = std::is_same<R, float>::value;
     const int col = tile + gridDim.y * blockIdx.z;
 
     if (tid == 0) {
@@ -398,6 +399,17 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     }
 
     R acc[5] = {0, 0, 0, 0, 0};
+    // packed observable sums (the two halves add up at the end): norm,
+    // energy and the three current components
+    float2 aN = f2s(0.f), aE = f2s(0.f), aJ[3] = {f2s(0.f), f2s(0.f), f2s(0.f)};
+    // occupations of the thread's orbitals, loop invariant
+    R fo[NVT][NC];
+    if constexpr (OBS) {
+#pragma unroll
+        for (int k = 0; k < NVT; ++k)
+#pragma unroll
+            for (int e = 0; e < NC; ++e) fo[k][e] = f[c0 / 2 + (vb + k) * NC + e];
+    }
     const int64_t plane_stride = (int64_t)G.nx * G.ny;
     int64_t g = (x0 + lx) + (int64_t)G.nx * (y0 + ly) + plane_stride * z0;
     const int64_t row = 2 * (int64_t)G.ld;
@@ -425,6 +437,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         const float4* s4 = ring + ((i + 4) % NSLOT) * Slot<VP>::N;    // plane z+2
         Cv<R> hw[NVT], dd[NVT][OBS ? 3 : 1];
         float2 hp[NVT][2];                  // packed path: h w of the vector's two complex values
+        float2 dlp[NVT][2][OBS ? 3 : 1];    // packed path with observables: gradient per axis
         if constexpr (FAST) {
             const float2 kk1 = f2s((float)G.kc1), kk2 = f2s((float)G.kc2);
             const float2 cd = f2s((float)(G.kc0 + sA[3] + vv));
@@ -451,15 +464,30 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                     float2 s1 = f2add(f2add(part(p1[0]), part(m1[0])), f2add(part(p1[1]), part(m1[1])));
                     s1 = f2add(s1, f2add(part(p1[2]), part(m1[2])));
                     float2 hk = f2mul(kk1, s1);
-                    float2 ha = f2mul(a1[0], f2sub(part(p1[0]), part(m1[0])));
-                    ha = f2fma(a1[1], f2sub(part(p1[1]), part(m1[1])), ha);
-                    ha = f2fma(a1[2], f2sub(part(p1[2]), part(m1[2])), ha);
+                    float2 ha;
+                    if constexpr (OBS) {
+                        // gradient per axis, dl = gk1 (w+1 - w-1) + gk2 (w+2 - w-2), then A . dl
+#pragma unroll
+                        for (int ax = 0; ax < 3; ++ax) {
+                            float2 dl = f2mul(f2s((float)G.gk1), f2sub(part(p1[ax]), part(m1[ax])));
+                            if (ORDER == 4) dl = f2fma(f2s((float)G.gk2), f2sub(part(p2[ax]), part(m2[ax])), dl);
+                            dlp[k][h][ax] = dl;
+                        }
+                        ha = f2mul(f2s((float)sA[0]), dlp[k][h][0]);
+                        ha = f2fma(f2s((float)sA[1]), dlp[k][h][1], ha);
+                        ha = f2fma(f2s((float)sA[2]), dlp[k][h][2], ha);
+                    } else {
+                        ha = f2mul(a1[0], f2sub(part(p1[0]), part(m1[0])));
+                        ha = f2fma(a1[1], f2sub(part(p1[1]), part(m1[1])), ha);
+                        ha = f2fma(a1[2], f2sub(part(p1[2]), part(m1[2])), ha);
+                        if (ORDER == 4)
+#pragma unroll
+                            for (int ax = 0; ax < 3; ++ax) ha = f2fma(a2[ax], f2sub(part(p2[ax]), part(m2[ax])), ha);
+                    }
                     if (ORDER == 4) {
                         float2 s2 = f2add(f2add(part(p2[0]), part(m2[0])), f2add(part(p2[1]), part(m2[1])));
                         s2 = f2add(s2, f2add(part(p2[2]), part(m2[2])));
                         hk = f2fma(kk2, s2, hk);
-#pragma unroll
-                        for (int ax = 0; ax < 3; ++ax) ha = f2fma(a2[ax], f2sub(part(p2[ax]), part(m2[ax])), ha);
                     }
                     hk = f2fma(cd, part(q[k][2]), hk);
                     // h w = hk - i ha
@@ -574,6 +602,19 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 const float2 o0 = f2fma(gi2, swp(hp[k][0]), f2fma(gr2, hp[k][0], lo2(ps)));
                 const float2 o1 = f2fma(gi2, swp(hp[k][1]), f2fma(gr2, hp[k][1], hi2(ps)));
                 *(reinterpret_cast<float4*>(out + g * row + c0) + vb + k) = make_float4(o0.x, o0.y, o1.x, o1.y);
+                if constexpr (OBS) {
+                    // f |c|^2, f Re(c* h w) and f Re(c* (-i) dl_a), each as a packed
+                    // pair whose halves add up to the term
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 c = h == 0 ? lo2(q[k][2]) : hi2(q[k][2]);
+                        const float2 f2 = f2s((float)fo[k][h]), f2m = make_float2((float)fo[k][h], -(float)fo[k][h]);
+                        aN = f2fma(f2, f2mul(c, c), aN);
+                        aE = f2fma(f2, f2mul(c, hp[k][h]), aE);
+#pragma unroll
+                        for (int ax = 0; ax < 3; ++ax) aJ[ax] = f2fma(f2m, f2mul(c, swp(dlp[k][h][ax])), aJ[ax]);
+                    }
+                }
 #pragma unroll
                 for (int w = 0; w < 4; ++w) q[k][w] = q[k][w + 1];
                 continue;
@@ -602,12 +643,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 unpack(q[k][2], c);
 #pragma unroll
                 for (int e = 0; e < NC; ++e) {
-                    const R fo = f[c0 / 2 + (vb + k) * NC + e];
                     const R cr = c.re[e], ci = c.im[e];
-                    acc[0] += fo * (cr * cr + ci * ci);
-                    acc[1] += fo * (cr * hw[k].re[e] + ci * hw[k].im[e]);
+                    acc[0] += fo[k][e] * (cr * cr + ci * ci);
+                    acc[1] += fo[k][e] * (cr * hw[k].re[e] + ci * hw[k].im[e]);
 #pragma unroll
-                    for (int ax = 0; ax < 3; ++ax) acc[2 + ax] += fo * (cr * dd[k][ax].im[e] - ci * dd[k][ax].re[e]);
+                    for (int ax = 0; ax < 3; ++ax)
+                        acc[2 + ax] += fo[k][e] * (cr * dd[k][ax].im[e] - ci * dd[k][ax].re[e]);
                 }
             }
 #pragma unroll
@@ -624,6 +665,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         }
     }
     if constexpr (OBS) {
+        if constexpr (FAST) {
+            acc[0] = aN.x + aN.y;
+            acc[1] = aE.x + aE.y;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) acc[2 + ax] = aJ[ax].x + aJ[ax].y;
+        }
         __shared__ double sh[NT / 32][5];
         const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
