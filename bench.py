@@ -49,6 +49,9 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle sample")
     p.add_argument("--ks", nargs=3, metavar=("N", "N_ORB", "MODE"),
                    help="time the Eq. 5 KS-space nonlocal correction on an N^3 x N_ORB complex64 domain in gemm MODE")
+    p.add_argument("--occ", nargs=3, metavar=("N", "N_ORB", "MODE"),
+                   help="time the shadow-dynamics occupations (overlap with Psi(0) and the f_s sums) on an "
+                        "N^3 x N_ORB complex64 domain in gemm MODE")
     p.add_argument("--reorth", nargs=3, metavar=("N", "N_ORB", "MODE"),
                    help="time Cholesky re-orthonormalisations of an N^3 x N_ORB complex64 domain in gemm MODE")
     p.add_argument("--gram", nargs=3, metavar=("N", "N_ORB", "MODE"),
@@ -347,7 +350,8 @@ def _device_orbitals(n_grid, n_orb, dV, seed, dtype):
     rdt = torch.float32 if dtype == torch.complex64 else torch.float64
     re = torch.randn(n_grid, n_orb, generator=g, device="cuda", dtype=rdt)
     im = torch.randn(n_grid, n_orb, generator=g, device="cuda", dtype=rdt)
-    return (torch.complex(re, im) / float(np.sqrt(n_grid * dV))).contiguous()
+    # E|re + i im|^2 = 2 per point
+    return (torch.complex(re, im) / float(np.sqrt(2.0 * n_grid * dV))).contiguous()
 
 
 def run_suite(args):
@@ -500,6 +504,37 @@ def run_ks(args):
     d.close()
 
 
+def run_occ(args):
+    """Time mlmd_occupations (C = dV Psi(0)^H Psi(t) as one real-embedded
+    GEMM of 2 (2 ld)^2 N_g flops times the split mode's products, then the
+    FP64 occupation sums on the device) on an N^3 x N_ORB complex64 domain."""
+    import torch
+    from paper_2509_00966_gb300 import build, mlmd
+    build.build()
+    n, no, mode = int(args.occ[0]), int(args.occ[1]), args.occ[2]
+    h = 0.35
+    d = mlmd.Domain((n, n, n), h, no, 4, "c64", gemm_mode=mode)
+    d.set_occupations(np.full(no, 2.0))
+    d.set_orbitals(_device_orbitals(n ** 3, no, h ** 3, 2, torch.complex64))
+    d.reorthonormalize("chol")
+    d.set_orbitals(d.get_orbitals())             # orthonormal reference Psi(0)
+    d.ks_correction(0.01 - 0.005j)               # Psi(t) = (1 - delta) Psi(0): n_exc = 2 N_o (1 - |1 - delta|^2)
+    d.occupations()
+    ms, (fs, nx) = _timed(lambda: d.occupations(), reps=5)
+    ld = (no + 7) // 8 * 8
+    nprod = {"bf16": 1, "bf16x2": 3, "bf16x3": 6, "fp16": 1, "fp32": 1}[mode]
+    flops = 2.0 * (2 * ld) ** 2 * n ** 3 * nprod
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    print(json.dumps({"kernel": "occupations (overlap GEMM + FP64 sums)", "grid": n, "n_orb": no, "mode": mode,
+                      "ms": ms, "tensor_tflops": flops / (ms * 1e-3) / 1e12, "peak_bf16_tflops": peak,
+                      "frac": flops / (ms * 1e-3) / 1e12 / peak, "n_exc": nx}), flush=True)
+    d.close()
+
+
 def run_reorth(args):
     """Time mlmd_reorthonormalize (FP64 Cholesky on the device, Gram and
     update GEMMs in the given gemm mode) on an N^3 x N_ORB complex64 domain
@@ -529,6 +564,8 @@ def main():
         run_reorth(args)
     elif args.ks:
         run_ks(args)
+    elif args.occ:
+        run_occ(args)
     elif args.suite:
         run_suite(args)
     else:

@@ -188,6 +188,19 @@ MLMD_API mlmd_status mlmd_reorthonormalize(mlmd_domain_t dom, int32_t kind);
  * (the per-domain n_exc of Sec. V.A.8). */
 MLMD_API mlmd_status mlmd_excitation(mlmd_domain_t dom, double* n_exc);
 
+/* Shadow-dynamics occupations (Sec. V.A.3-4: LFD hands the occupation
+ * numbers of the Kohn-Sham states back to QXMD; Sec. V.A.8: n_exc per domain
+ * is computed from them).  The reference orbitals psi_s(0) from
+ * mlmd_set_orbitals are the adiabatic states; the current orbitals psi_n(t)
+ * carry the occupations f_n of mlmd_set_occupations.  f_out: host double
+ * [N_o], f_s(t) = sum_n f_n |<psi_s(0)|psi_n(t)>|^2 (may be NULL).  n_exc:
+ * host double, sum_n f_n - sum_s f_s(t), the electrons that have left the
+ * span of the reference orbitals (may be NULL; with every f_n = 2 it equals
+ * mlmd_excitation).  The overlap runs as a GEMM in the domain's gemm_mode;
+ * the sums run on the device in FP64 in a fixed order.  MLMD_ERR_INVALID if
+ * both outputs are NULL, MLMD_ERR_STATE without reference orbitals. */
+MLMD_API mlmd_status mlmd_occupations(mlmd_domain_t dom, double* f_out, double* n_exc);
+
 /* KS-space nonlocal correction of Eq. 5 (Sec. V.B.5) applied once to the
  * current orbitals: Psi(t) <- Psi(t) - delta Psi(0) C with C = dV Psi(0)^H
  * Psi(t), the overlap with the reference orbitals from mlmd_set_orbitals in

@@ -592,20 +592,46 @@ mlmd_status mlmd_reorthonormalize(mlmd_domain_t d, int32_t kind) {
     });
 }
 
+// C = dV Psi(0)^H Psi(t) and its occupation sums on the device; fills
+// fs (device [n_orb]) and tot (device [2], see launch_occupations).
+static void reference_occupations(Domain& d, double** fs, double** tot) {
+    const int n = d.desc.n_orb;
+    double* base = ensure_dense(d, (size_t)n * n * 2 + 2 * (size_t)n + 2);
+    double* C = base;
+    *fs = base + (size_t)n * n * 2;
+    double* rs = *fs + n;
+    *tot = rs + n;
+    launch_overlap(d, d.psi0, d.psi, d.desc.h * d.desc.h * d.desc.h, C);
+    launch_occupations(d, C, *fs, rs, *tot);
+}
+
 mlmd_status mlmd_excitation(mlmd_domain_t d, double* n_exc) {
     return guarded(d, [&] {
         MLMD_REQUIRE(n_exc != nullptr, MLMD_ERR_INVALID, "null output");
         MLMD_REQUIRE(d->psi0_valid, MLMD_ERR_STATE, "no reference orbitals (call mlmd_set_orbitals)");
-        const int n = d->desc.n_orb;
-        double* C = ensure_dense(*d, (size_t)n * n * 2);
-        launch_overlap(*d, d->psi0, d->psi, d->desc.h * d->desc.h * d->desc.h, C);
-        std::vector<double> h((size_t)n * n * 2);
-        MLMD_CUDA(cudaMemcpyAsync(h.data(), C, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, d->stream));
+        double *fs = nullptr, *tot = nullptr;
+        reference_occupations(*d, &fs, &tot);
+        double t[2];
+        MLMD_CUDA(cudaMemcpyAsync(t, tot, sizeof(t), cudaMemcpyDeviceToHost, d->stream));
         MLMD_CUDA(cudaStreamSynchronize(d->stream));
         check_err_flag(*d);
-        double s = 0.0;
-        for (size_t i = 0; i < h.size(); ++i) s += h[i] * h[i];
-        *n_exc = 2.0 * ((double)n - s);
+        *n_exc = 2.0 * ((double)d->desc.n_orb - t[1]);
+    });
+}
+
+mlmd_status mlmd_occupations(mlmd_domain_t d, double* f_out, double* n_exc) {
+    return guarded(d, [&] {
+        MLMD_REQUIRE(f_out != nullptr || n_exc != nullptr, MLMD_ERR_INVALID, "no output");
+        MLMD_REQUIRE(d->psi0_valid, MLMD_ERR_STATE, "no reference orbitals (call mlmd_set_orbitals)");
+        double *fs = nullptr, *tot = nullptr;
+        reference_occupations(*d, &fs, &tot);
+        double t[2];
+        if (f_out)
+            MLMD_CUDA(cudaMemcpyAsync(f_out, fs, sizeof(double) * d->desc.n_orb, cudaMemcpyDeviceToHost, d->stream));
+        MLMD_CUDA(cudaMemcpyAsync(t, tot, sizeof(t), cudaMemcpyDeviceToHost, d->stream));
+        MLMD_CUDA(cudaStreamSynchronize(d->stream));
+        check_err_flag(*d);
+        if (n_exc) *n_exc = t[0];
     });
 }
 

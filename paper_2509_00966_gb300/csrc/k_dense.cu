@@ -507,6 +507,68 @@ void launch_scale_complex(Domain& d, double* M, int64_t nn, double sr, double si
     MLMD_CUDA(cudaGetLastError());
 }
 
+// Occupations of the reference orbitals (Sec. V.A.3, V.A.8) from the
+// overlap C[s][m] = <psi_s(0)|psi_m(t)> (complex double [n][n]): one warp
+// per row s, fs[s] = sum_m f_m |C_sm|^2 and rs[s] = sum_m |C_sm|^2, lanes
+// striding over m, then a butterfly (a fixed order, so the sums repeat
+// bit for bit).
+__global__ void k_occ_rows(const double* __restrict__ C, const double* __restrict__ f, int n,
+                           double* __restrict__ fs, double* __restrict__ rs) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= n) return;
+    const double* row = C + (int64_t)2 * s * n;
+    double af = 0.0, a1 = 0.0;
+    for (int m = lane; m < n; m += 32) {
+        const double re = row[2 * m], im = row[2 * m + 1];
+        const double p = re * re + im * im;
+        af += f[m] * p;
+        a1 += p;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        af += __shfl_xor_sync(0xffffffffu, af, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+    if (lane == 0) {
+        fs[s] = af;
+        rs[s] = a1;
+    }
+}
+
+// out[0] = sum_m f_m - sum_s fs[s] (n_exc), out[1] = sum_s rs[s]; one block,
+// thread-strided partials then a shared-memory tree (fixed order).
+__global__ void k_occ_total(const double* __restrict__ fs, const double* __restrict__ rs,
+                            const double* __restrict__ f, int n, double* __restrict__ out) {
+    __shared__ double sh[2][256];
+    double a = 0.0, b = 0.0;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        a += f[s] - fs[s];
+        b += rs[s];
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0];
+        out[1] = sh[1][0];
+    }
+}
+
+void launch_occupations(Domain& d, const double* C, double* fs, double* rs, double* out) {
+    const int n = d.desc.n_orb;
+    k_occ_rows<<<(n + 7) / 8, 256, 0, d.stream>>>(C, d.f, n, fs, rs);
+    k_occ_total<<<1, 256, 0, d.stream>>>(fs, rs, d.f, n, out);
+    d.launches += 2;
+    MLMD_CUDA(cudaGetLastError());
+}
+
 void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info) {
     const int n = d.desc.n_orb;
     MLMD_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), d.stream));

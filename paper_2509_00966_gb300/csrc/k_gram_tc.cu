@@ -8,9 +8,13 @@
 // Each FP32 operand x is split into 16-bit parts: BF16 (x ~ x0), BF16X2
 // (x ~ x0 + x1, products 00, 01, 10), BF16X3 (x ~ x0 + x1 + x2, products with
 // i + j <= 2: 00, 01, 10, 02, 11, 20 -- the split-product scheme of Henry, Tang
-// and Heinecke, ARITH 2019) or FP16 after a power-of-two scale.  All products
-// of a tile accumulate in FP32 in tensor memory; K-slices of the grid go to
-// different CTAs and their FP32 tiles are summed in FP64.
+// and Heinecke, ARITH 2019) or FP16 after a power-of-two scale.  The products
+// accumulate in FP32 in tensor memory in short runs (about 24 MMAs): the
+// tensor core's FP32 accumulation rounds towards zero, so one run over a
+// whole K-slice of 10^5 grid points biased the diagonal of S by about 5e-4;
+// drain warps add each run into FP32 running sums in registers (rounded to
+// nearest), and K-slices of the grid go to different CTAs whose tiles are
+// summed in FP64.
 //
 // Structure: a split pass converts each FP32 operand once into its 16-bit
 // parts, stored pre-tiled in device memory: every 128-column x 64-point tile
@@ -20,9 +24,10 @@
 // over a K range: thread 0 streams the tiles with one bulk copy each into a
 // ring of shared-memory stages (full / empty mbarriers), thread 32 issues
 // the tcgen05.mma instructions (M = N = 128, K = 16, FP32 accumulator in
-// tensor memory) and frees each stage with tcgen05.commit, and the four
-// warps read the accumulator with tcgen05.ld, pair rows 2a / 2a+1 with a lane
-// shuffle and write the complex FP64 partial tile.  For a Gram of one array
+// tensor memory, two accumulator buffers used in turn, one per run) and frees
+// each stage with tcgen05.commit, and warps 2-5 read each finished run with
+// tcgen05.ld into their running sums (filled / drained mbarriers), then pair
+// rows 2a / 2a+1 with a lane shuffle and write the complex FP64 partial tile.  For a Gram of one array
 // with itself only the upper-triangular tiles are computed.  Every mbarrier
 // wait is bounded; tensor memory is always freed.
 #include <cuda_bf16.h>
@@ -75,20 +80,30 @@ __global__ void __launch_bounds__(256) k_split_tiles(const float* __restrict__ X
     }
 }
 
+// K-steps (BK grid points each) per accumulation run: about 24 MMAs
+template <int MODE> struct RunSteps {
+    static constexpr int value = (24 / (Split<MODE>::NPROD * KSTEPS_PER_MMA)) > 0
+                                     ? 24 / (Split<MODE>::NPROD * KSTEPS_PER_MMA) : 1;
+};
+
 // part[z][n][m] (complex FP64) for the real output tile (ta, tb) of G = Xr^T Yr
 // over K-slice z.  Thread 0 feeds a ring of STAGES buffers with bulk copies
-// of the pre-split tiles; thread 32 issues the MMAs and frees each buffer
-// with a commit; all four warps read the accumulator at the end.  tri != 0:
+// of the pre-split tiles; thread 32 issues the MMAs, frees each buffer with
+// a commit and closes each run of RunSteps K-steps with a commit to
+// filled[b] (runs alternate between the two accumulators b = 0, 1); warps
+// 2-5 add each finished run to their FP32 running sums and arrive on
+// drained[b] so the accumulator can take the run after next.  tri != 0:
 // blockIdx.x enumerates the upper-triangular tile pairs (ta <= tb).
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     k_gram_tc(const unsigned char* __restrict__ pa, const unsigned char* __restrict__ pb, int nmt, int nks,
               int ks_per_split, int n_orb, int tri, double unscale, double* __restrict__ part, int* __restrict__ err) {
     constexpr int NPART = Split<MODE>::NPART, NPROD = Split<MODE>::NPROD, STAGES = Stages<MODE>::value;
+    constexpr int RUN = RunSteps<MODE>::value;
     constexpr uint32_t STAGE_BYTES = 2 * NPART * kTileBytes;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], filled[2], drained[2], done;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_sh;
 
@@ -105,10 +120,11 @@ __global__ void __launch_bounds__(128, 1)
     }
     const int ks0 = blockIdx.y * ks_per_split;
     const int nsteps = min(ks_per_split, nks - ks0);
+    const int nruns = (nsteps + RUN - 1) / RUN;
 
-    if (warp == 0) {
+    if (warp == 0) {     // two 128-column FP32 accumulators
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(128u)
+                     "r"(256u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -116,6 +132,10 @@ __global__ void __launch_bounds__(128, 1)
         for (int st = 0; st < STAGES; ++st) {
             mbar_init(&full[st], 1);
             mbar_init(&empty[st], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&filled[b], 1);
+            mbar_init(&drained[b], 4);       // one arrival per drain warp
         }
         mbar_init(&done, 1);
         abort_sh = 0;
@@ -126,6 +146,8 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     constexpr uint32_t IDESC = instr_desc(MODE == MLMD_GEMM_FP16 ? 0u : 1u);
+    bool drained_all = false;            // drain warps: every run is in the sums
+    float sum[BN];                       // drain warps: running sums of one tile row
 
     if (tid == 0) {                     // producer
         for (int i = 0; i < nsteps && !abort_sh; ++i) {
@@ -148,6 +170,13 @@ __global__ void __launch_bounds__(128, 1)
         }
     } else if (tid == 32) {             // MMA issuer
         for (int i = 0; i < nsteps; ++i) {
+            const int run = i / RUN, b = run & 1;
+            const bool first = (i % RUN) == 0;
+            // the run before last in this accumulator must have been drained
+            if (first && run >= 2 && !mbar_wait_bounded(&drained[b], (uint32_t)((run / 2 - 1) & 1))) {
+                abort_sh = 1;
+                break;
+            }
             const int st = i % STAGES;
             if (!mbar_wait_bounded(&full[st], (uint32_t)((i / STAGES) & 1))) {
                 abort_sh = 1;
@@ -156,20 +185,46 @@ __global__ void __launch_bounds__(128, 1)
             tc_fence_after();
             const uint32_t As = smem_u32(smem + st * STAGE_BYTES);
             const uint32_t Bs = As + NPART * kTileBytes;
+            const uint32_t acc = tmem + (uint32_t)(b * BN);
 #pragma unroll
             for (int p = 0; p < NPROD; ++p)
 #pragma unroll
                 for (int kk = 0; kk < KSTEPS_PER_MMA; ++kk) {
                     const uint64_t ad = smem_desc(As + prod_a(p) * kTileBytes + kk * 256, 128, 1024);
                     const uint64_t bd = smem_desc(Bs + prod_b(p) * kTileBytes + kk * 256, 128, 1024);
-                    mma_f16(tmem, ad, bd, IDESC, (i > 0 || p > 0 || kk > 0) ? 1u : 0u);
+                    mma_f16(acc, ad, bd, IDESC, (first && p == 0 && kk == 0) ? 0u : 1u);
                 }
             mma_commit(&empty[st]);
+            if ((i % RUN) == RUN - 1 || i == nsteps - 1) mma_commit(&filled[b]);
         }
         mma_commit(&done);              // all MMAs issued above have completed when this fires
+    } else if (warp >= 2) {             // drain warps: TMEM lanes 32 (warp % 4) .. +31
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+#pragma unroll
+        for (int c = 0; c < BN; ++c) sum[c] = 0.f;
+        int r = 0;
+        for (; r < nruns; ++r) {
+            const int b = r & 1;
+            if (!mbar_wait_bounded(&filled[b], (uint32_t)((r / 2) & 1))) {
+                abort_sh = 1;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int cb = 0; cb < BN; cb += 32) {
+                float v[32];
+                tmem_ld32(tmem + lanes + (uint32_t)(b * BN + cb), v);
+#pragma unroll
+                for (int cc = 0; cc < 32; ++cc) sum[cb + cc] += v[cc];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&drained[b]);
+        }
+        drained_all = r == nruns;
     }
     __syncthreads();
-    if (!abort_sh && nsteps > 0 && !mbar_wait_bounded(&done, 0)) abort_sh = 1;
+    if (nsteps > 0 && !mbar_wait_bounded(&done, 0)) abort_sh = 1;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -179,24 +234,20 @@ __global__ void __launch_bounds__(128, 1)
             // let bulk copies still in flight land (bounded)
             for (int st = 0; st < STAGES; ++st) (void)mbar_wait_bounded(&full[st], 0);
         }
-    } else if (nsteps > 0) {
-        // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (rows of the tile)
-        const int row = ta * BM + warp * 32 + lane;                   // real row of G
-        for (int cb = 0; cb < BN; cb += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+    } else if (warp >= 2 && drained_all && nsteps > 0) {
+        // row of G held by this lane; rows 2a and 2a+1 sit in neighbouring lanes
+        const int row = ta * BM + (warp & 3) * 32 + lane;
 #pragma unroll
-            for (int cc = 0; cc < 32; cc += 2) {
-                const float ee = v[cc], eo = v[cc + 1];                 // G[row][2b], G[row][2b+1]
-                const float oe = __shfl_xor_sync(0xffffffffu, ee, 1);  // the partner row's
-                const float oo = __shfl_xor_sync(0xffffffffu, eo, 1);
-                if ((lane & 1) == 0) {
-                    const int n = row >> 1, m = (tb * BN + cb + cc) >> 1;
-                    if (n < n_orb && m < n_orb) {
-                        double* dst = part + (((int64_t)blockIdx.y * n_orb + n) * n_orb + m) * 2;
-                        dst[0] = unscale * ((double)ee + (double)oo);
-                        dst[1] = unscale * ((double)eo - (double)oe);
-                    }
+        for (int cc = 0; cc < BN; cc += 2) {
+            const float ee = sum[cc], eo = sum[cc + 1];                 // G[row][2b], G[row][2b+1]
+            const float oe = __shfl_xor_sync(0xffffffffu, ee, 1);      // the partner row's
+            const float oo = __shfl_xor_sync(0xffffffffu, eo, 1);
+            if ((lane & 1) == 0) {
+                const int n = row >> 1, m = (tb * BN + cc) >> 1;
+                if (n < n_orb && m < n_orb) {
+                    double* dst = part + (((int64_t)blockIdx.y * n_orb + n) * n_orb + m) * 2;
+                    dst[0] = unscale * ((double)ee + (double)oo);
+                    dst[1] = unscale * ((double)eo - (double)oe);
                 }
             }
         }
@@ -205,7 +256,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
     }
 }
 
@@ -252,7 +303,7 @@ void gram_mode(Domain& d, const float* X, const float* Y, double scale, double* 
     double* part = (double*)d.mem.get((size_t)nsplit * no * no * 2 * sizeof(double));
     constexpr uint32_t smem = STAGES * 2 * NPART * kTileBytes + 1024;
     ensure_dynamic_smem(reinterpret_cast<const void*>(k_gram_tc<MODE>), smem);
-    k_gram_tc<MODE><<<dim3(tiles, nsplit), 128, smem, d.stream>>>(pa, pb, nmt, nks, ks_per_split, no, same ? 1 : 0,
+    k_gram_tc<MODE><<<dim3(tiles, nsplit), 192, smem, d.stream>>>(pa, pb, nmt, nks, ks_per_split, no, same ? 1 : 0,
                                                                   unscale, part, d.err_flag);
     const int64_t nn = (int64_t)no * no;
     k_gram_reduce<<<(int)std::min<int64_t>((nn + 255) / 256, 2048), 256, 0, d.stream>>>(part, nsplit, no, same ? 1 : 0,

@@ -239,6 +239,10 @@ bool launch_overlap_tc(Domain& d, const void* X, const void* Y, double scale, do
 // Y[g][m] = sum_n X[g][n] M[n][m] (M complex double [n_orb][n_orb], device)
 // Y = Z + X M (Z = null: Y = X M), SIMT, FP32 or FP64 accumulation per the domain.
 void launch_update(Domain& d, const void* X, const double* M, void* Y, const void* Z = nullptr);
+// From C[s][m] = <psi_s(0)|psi_m(t)> (device complex double [n_orb][n_orb]):
+// fs[s] = sum_m f_m |C_sm|^2, rs[s] = sum_m |C_sm|^2 (device [n_orb]) and
+// out[0] = sum f - sum fs, out[1] = sum rs (device [2]); FP64, fixed order.
+void launch_occupations(Domain& d, const double* C, double* fs, double* rs, double* out);
 // M <- (sr + i si) M for a complex FP64 matrix of nn entries.
 void launch_scale_complex(Domain& d, double* M, int64_t nn, double sr, double si);
 // Y = X M on the tensor cores in the domain's split mode (c64, non-FP32 GEMM

@@ -65,6 +65,7 @@ _SIGS = {
     "mlmd_overlap": (ctypes.c_int, [_P, _P]),
     "mlmd_reorthonormalize": (ctypes.c_int, [_P, ctypes.c_int32]),
     "mlmd_excitation": (ctypes.c_int, [_P, _P]),
+    "mlmd_occupations": (ctypes.c_int, [_P, _P, _P]),
     "mlmd_ks_correction": (ctypes.c_int, [_P, _P]),
     "mlmd_propagate_adjoint": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32]),
     "mlmd_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.POINTER(_P)]),
@@ -239,6 +240,15 @@ def excitation(h):
     return v.value
 
 
+def occupations(h, n_orb):
+    """(f_s(t) [N_o], n_exc): occupations of the reference orbitals and the
+    electrons that left their span."""
+    fs = np.zeros(n_orb, np.float64)
+    v = ctypes.c_double()
+    _check(lib().mlmd_occupations(h, ctypes.c_void_p(fs.ctypes.data), ctypes.byref(v)), h)
+    return fs, v.value
+
+
 def ks_correction(h, delta):
     """Eq. 5 once: Psi(t) -= delta Psi(0) (dV Psi(0)^H Psi(t)); delta complex."""
     dl = np.array([complex(delta).real, complex(delta).imag], np.float64)
@@ -409,6 +419,9 @@ class Domain:
 
     def ks_correction(self, delta):
         ks_correction(self.handle, delta)
+
+    def occupations(self):
+        return occupations(self.handle, self.n_orb)
 
     def propagate_adjoint(self, A, ckpt_every, dL_dV=None):
         return propagate_adjoint(self.handle, A, ckpt_every, self.n_grid, dL_dV)

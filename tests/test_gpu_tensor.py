@@ -151,3 +151,81 @@ def test_ks_correction_needs_reference_orbitals():
     with pytest.raises(mlmd.MLMDError):
         d.ks_correction(0.1)
     d.close()
+
+
+@pytest.mark.parametrize("precision,mode,tol", [("c128", "fp32", 1e-12), ("c64", "fp32", 2e-6), ("c64", "bf16x3", 2e-5),
+                                                ("c64", "bf16x2", 1e-4), ("c64", "fp16", 2e-3), ("c64", "bf16", 1e-2)])
+@pytest.mark.parametrize("n,n_orb", [((12, 10, 14), 37), ((16, 16, 16), 150)])
+def test_occupations(precision, mode, tol, n, n_orb):
+    """Shadow-dynamics occupations through mlmd_occupations (overlap GEMM in
+    the domain's mode, FP64 sums on the device) against the oracle on the
+    same Psi(0) and Psi(t), with unequal occupations f_n.  The error of
+    f_s = sum_n f_n |C_sn|^2 is at most 2 max(f) sqrt(N_o) times the error
+    of the overlap entries (tol, relative to max |C| = 1)."""
+    spec = small_spec(precision=precision, n=n, n_orb=n_orb, steps=6, dt=0.05)
+    d, V = gpu_domain(spec, gemm_mode=mode)
+    f = np.random.default_rng(4).uniform(0.2, 2.0, n_orb)
+    d.set_occupations(f)
+    psi0 = orbitals(spec)
+    d.set_orbitals(to_device(psi0, precision))
+    fs0, n0 = d.occupations()                  # Psi(t) = Psi(0): every state keeps its occupation
+    bound = 2 * f.max() * np.sqrt(n_orb) * tol
+    assert np.max(np.abs(fs0 - f)) <= bound and abs(n0) <= n_orb * bound, (mode, np.max(np.abs(fs0 - f)), n0)
+    d.propagate(spec.A)
+    psit = to_numpy(d.get_orbitals())
+    p0 = to_numpy(to_device(psi0, precision))  # Psi(0) as the domain holds it
+    fs, nx = d.occupations()
+    rfs, rnx = oracle.occupations(p0, psit, f, spec.dV)
+    assert rnx > 10 * bound, (mode, rnx)          # the orbitals have left the reference span
+    assert np.max(np.abs(fs - rfs)) <= bound, (mode, np.max(np.abs(fs - rfs)))
+    assert abs(nx - rnx) <= n_orb * bound, (mode, nx, rnx)
+    # with every f_n = 2 the count is mlmd_excitation's
+    d.set_occupations(np.full(n_orb, 2.0))
+    _, n2 = d.occupations()
+    assert abs(n2 - d.excitation()) <= 1e-10 * n_orb
+    d.close()
+
+
+def test_occupations_arguments():
+    from paper_2509_00966_gb300 import mlmd
+    spec = small_spec(precision="c64", steps=1)
+    d, V = gpu_domain(spec, gemm_mode="bf16x3")
+    with pytest.raises(mlmd.MLMDError):         # no reference orbitals yet
+        d.occupations()
+    d.set_orbitals(to_device(orbitals(spec), "c64"))
+    assert mlmd.lib().mlmd_occupations(d.handle, None, None) == 1   # MLMD_ERR_INVALID: no output
+    d.close()
+
+
+# FP16 is left out: plane waves repeat a few values, so its 11-bit operand
+# rounding is systematic per orbital (up to 5e-4 on a diagonal entry), which
+# the max |S - I| bound of the other tests covers
+@pytest.mark.parametrize("mode,bias_tol", [("bf16x3", 1e-5), ("bf16x2", 1e-5)])
+def test_overlap_long_k_unbiased(mode, bias_tol):
+    """Over a long K range (48^3 grid points, 1024 orbitals, so each CTA runs
+    hundreds of K-steps) the overlap of exactly orthonormal orbitals -- grid
+    plane waves, orthonormal by the discrete Fourier sum -- must stay
+    unbiased to FP32 class: the tensor core's FP32 accumulation rounds
+    towards zero, and one accumulation run per K-slice pulled the diagonal
+    of S down by about 1e-4 here (5e-4 at 64^3).  With runs of about 24 MMAs
+    drained into round-to-nearest sums the mean diagonal is 1 - 3e-6 in
+    BF16X3."""
+    import torch
+    from paper_2509_00966_gb300 import mlmd
+    n, no, h = 48, 1024, 0.35
+    ng, dV = n ** 3, h ** 3
+    m = np.array([(a, b, c) for a in range(-8, 8) for b in range(-4, 4) for c in range(-4, 4)], np.float64)
+    assert len(m) == no
+    idx = np.arange(ng)
+    x, y, z = idx % n, (idx // n) % n, idx // (n * n)
+    d = mlmd.Domain((n, n, n), h, no, 4, "c64", gemm_mode=mode)
+    xyz = torch.from_numpy(np.stack([x, y, z], 1).astype(np.float64)).cuda()
+    phase = (xyz @ torch.from_numpy(m.T).cuda()) * (2 * np.pi / n)
+    psi = (torch.polar(torch.ones_like(phase), phase) / np.sqrt(ng * dV)).to(torch.complex64).contiguous()
+    del phase, xyz
+    d.set_orbitals(psi)
+    S = d.overlap()
+    diag = np.real(np.diag(S))
+    assert abs(diag.mean() - 1.0) <= bias_tol, (mode, diag.mean() - 1.0)
+    assert np.abs(S - np.eye(no)).max() <= TOL[mode], (mode, np.abs(S - np.eye(no)).max())
+    d.close()
