@@ -35,6 +35,20 @@ FALLBACK_HBM_GBS = 6800.0
 # full-scheme passes in complex64: the first reads psi and writes w (16 B),
 # the other three read w and psi and write w or psi (24 B each)
 STAGE_BYTES_PER_UNIT = 16 + 3 * 24
+# DRAM bytes (read + write) per stage launch on this workload, the mean over
+# the four stage launches of one Taylor step (490 + 759 + 759 + 724 MB), from
+# one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum of the
+# current stage kernel in the tile shape the autotuner picks (128-byte
+# orbital chunks, 4 threads per point); the command is in
+# profiles/k_stage_tma_c1.md.  The algorithmic mean is 88 / 4 B x N_g N_o =
+# 622.9 MB: the 1.10x are the z halo planes and the scatter entry blocks.
+STAGE_TRAFFIC_BYTES_PER_LAUNCH = 683.1e6
+
+
+def _is_bench_workload(spec, args):
+    """The traffic figure was measured on the 48^3 x 256 domain with 64 x 4
+    projectors; other sizes report none."""
+    return spec.n == (48, 48, 48) and spec.n_orb == 256 and spec.n_proj == 4 and len(spec.atoms) == 64
 
 
 def _args():
@@ -314,7 +328,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_stage (fused stencil + V + A + scatter + Taylor combine)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_source": f"{peak_src} hbm_gbs",
-                     "bytes_per_unit_step": STAGE_BYTES_PER_UNIT, "traffic": None,
+                     "bytes_per_unit_step": STAGE_BYTES_PER_UNIT,
+                     "traffic": STAGE_TRAFFIC_BYTES_PER_LAUNCH if _is_bench_workload(spec, args) else None,
+                     "traffic_unit": "bytes per stage launch (ncu, mean of the four stage launches of a step)",
                      "kernel_share": {"stage": st_ms / t_ms, "project": pr_ms / t_ms},
                      "launches": {"stage": st_n, "project": pr_n}},
         "cpu_baseline": cpu,
