@@ -182,6 +182,27 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(x, ws):
+    """The largest x over the ranks (the slowest replica's time); x itself
+    on one rank.  Uses the process group's own device: CUDA under NCCL, the
+    host under gloo."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(ws, units_per_rank, t_s):
+    """Whole-job throughput of ws independent replicas (no data exchanged
+    between them): every rank processed units_per_rank, in at most the
+    slowest rank's time t_s."""
+    return ws * units_per_rank / t_s
+
+
 def _physical_gpu(local):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -277,10 +298,8 @@ def run_ours(args):
     pr_ms, pr_n = mlmd.profile_read(dom.handle, "project")
     mlmd.profile_enable(dom.handle, False)
     ck = clocks.stop()
+    t_ms = _max_over_ranks(t_ms, ws)
     if ws > 1:
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
         torch.distributed.barrier()
 
     # end to end through the C ABI with host buffers: h2d of the orbitals,
@@ -298,13 +317,10 @@ def run_ours(args):
         if k > 0:
             e2e_t.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e_t)) if e2e_t else float("nan")
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = _max_over_ranks(e2e_s, ws)
 
     units_step = spec.n_grid * spec.n_orb * args.qd_steps
-    value = ws * units_step * args.steps / (t_ms * 1e-3)
+    value = _job_value(ws, units_step * args.steps, t_ms * 1e-3)
     electrons = float(np.sum(spec.occ))
     t2s = (t_ms * 1e-3) / (args.steps * args.qd_steps * electrons)
     peak, peak_src = _peaks()
@@ -334,7 +350,7 @@ def run_ours(args):
                      "kernel_share": {"stage": st_ms / t_ms, "project": pr_ms / t_ms},
                      "launches": {"stage": st_n, "project": pr_n}},
         "cpu_baseline": cpu,
-        "e2e": {"value": ws * units_step / e2e_s, "unit": UNIT,
+        "e2e": {"value": _job_value(ws, units_step, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": int(psi.size * 8 + A.size * 8),
                 "d2h_bytes_per_step": int(psi.size * 8 + args.qd_steps * 5 * 8)},
         "gpu_launches": int(launches),
