@@ -1074,7 +1074,14 @@ void tma_build_nl(Domain& d, const double* D_host) {
     }
     // projection tables: projection columns of pzc planes, entries ordered by
     // (slot, plane, point); slots number a column's atoms in ascending order
-    t.pzc = std::min(4, t.zc);
+    // MLMD_PROJ_PLANES (1..16) overrides the 4 planes per projection column
+    // (profiling)
+    int pz = 4;
+    if (const char* e = std::getenv("MLMD_PROJ_PLANES")) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= 16) pz = v;
+    }
+    t.pzc = std::min(pz, t.zc);
     const int nzp = (d.desc.n[2] + t.pzc - 1) / t.pzc;
     const int64_t ncp = (int64_t)ntiles * nzp;
     auto pcol_of = [&](int64_t g) {
