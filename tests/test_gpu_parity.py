@@ -305,6 +305,45 @@ def test_c1_full_size_sampled_orbitals():
     d.close()
 
 
+def test_c2_full_size_sampled_orbitals_and_reorth():
+    """The precision-form workload at full size (64^3 grid, 1024 complex64
+    orbitals, 128 atoms x 8 projectors, BF16X3 GEMMs, re-orthonormalisation
+    every 10 steps).  For 9 steps no re-orthonormalisation couples the
+    orbitals, so the oracle runs a sample of them; then one BF16X3 Cholesky
+    re-orthonormalisation of all 1024, whose result must be orthonormal as
+    an independent FP32 SIMT overlap measures it.  The orbitals are seeded
+    random vectors made on the device, each normalised."""
+    import torch
+    from paper_2509_00966_gb300 import mlmd
+    spec = inputs.config("c2", n_steps=9)
+    d, V = gpu_domain(spec, gemm_mode="bf16x3", ortho_every=10)
+    g = torch.Generator(device="cuda").manual_seed(2)
+    re = torch.randn(spec.n_grid, spec.n_orb, generator=g, device="cuda")
+    im = torch.randn(spec.n_grid, spec.n_orb, generator=g, device="cuda")
+    psi = torch.complex(re, im)
+    del re, im
+    psi = (psi / torch.sqrt(spec.dV * (psi.abs() ** 2).sum(0, keepdim=True))).contiguous()
+    sample = [0, 333, 700, 1023]
+    p0 = psi[:, sample].cpu().numpy().astype(np.complex128)
+    d.set_orbitals(psi)
+    del psi
+    d.propagate(spec.A, obs=False)
+    out = d.get_orbitals()[:, sample].cpu().numpy().astype(np.complex128)
+    od = oracle_domain(spec, V, n_orb=len(sample))
+    ref, _ = oracle.propagate(od, p0, spec.A, spec.dt, np.full(len(sample), 2.0))
+    assert np.max(np.abs(out - ref)) <= 1e-5, np.max(np.abs(out - ref))
+    d.reorthonormalize("chol")
+    q = d.get_orbitals()
+    d.close()
+    d32 = mlmd.Domain(spec.n, spec.h, spec.n_orb, spec.fd_order, "c64", gemm_mode="fp32", dt=spec.dt)
+    d32.set_orbitals(q)
+    del q
+    S = d32.overlap()
+    d32.close()
+    err = np.abs(S - np.eye(spec.n_orb))
+    assert err.max() <= 2e-5 and abs(np.real(np.diag(S)).mean() - 1.0) <= 1e-5, (err.max(), np.diag(S).mean())
+
+
 def test_zero_steps_and_single_orbital():
     spec = small_spec(precision="c128", n_orb=1, steps=4)
     out, obs, ref, robs = _run_both(spec)
