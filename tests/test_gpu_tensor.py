@@ -207,7 +207,7 @@ def test_overlap_long_k_unbiased(mode, bias_tol):
     plane waves, orthonormal by the discrete Fourier sum -- must stay
     unbiased to FP32 class: the tensor core's FP32 accumulation rounds
     towards zero, and one accumulation run per K-slice pulled the diagonal
-    of S down by about 1e-4 here (5e-4 at 64^3).  With runs of about 24 MMAs
+    of S down (by 5e-4 measured at 64^3 x 1024; an estimated 1.4e-4 here).  With runs of about 24 MMAs
     drained into round-to-nearest sums the mean diagonal is 1 - 3e-6 in
     BF16X3."""
     import torch
