@@ -207,9 +207,9 @@ def test_overlap_long_k_unbiased(mode, bias_tol):
     plane waves, orthonormal by the discrete Fourier sum -- must stay
     unbiased to FP32 class: the tensor core's FP32 accumulation rounds
     towards zero, and one accumulation run per K-slice pulled the diagonal
-    of S down (by 5e-4 measured at 64^3 x 1024; an estimated 1.4e-4 here).  With runs of about 24 MMAs
-    drained into round-to-nearest sums the mean diagonal is 1 - 3e-6 in
-    BF16X3."""
+    of S down (by 5e-4 measured at 64^3 x 1024; an estimated 1.4e-4 here).
+    With runs of about 24 MMAs drained into round-to-nearest sums the mean
+    diagonal is 1 - 3e-6 in BF16X3."""
     import torch
     from paper_2509_00966_gb300 import mlmd
     n, no, h = 48, 1024, 0.35
