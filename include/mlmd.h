@@ -64,14 +64,19 @@ typedef enum {
 
 enum { MLMD_C128 = 0, MLMD_C64 = 1 };
 
-/* Arithmetic of the nonlocal projection/scatter GEMMs and of the Gram
- * (overlap) GEMM for MLMD_C64 domains (Sec. V.B.7, Sec. VI.C):
- *   FP32    plain FP32 products and sums;
+/* Arithmetic of the orbital-space GEMMs of MLMD_C64 domains (Sec. V.B.7,
+ * Sec. VI.C): the overlap Psi^H Psi or Psi(0)^H Psi (re-orthonormalisation,
+ * mlmd_overlap, mlmd_excitation, mlmd_occupations, Eq. 5) and the orbital
+ * updates Psi M (re-orthonormalisation, Eq. 5).  The split modes run on the
+ * tensor cores:
+ *   FP32    plain FP32 products and sums (SIMT);
  *   BF16    each FP32 operand rounded to one bf16, FP32 accumulation;
  *   BF16X2  operand = two bf16 parts, 3 cross products, FP32 accumulation;
  *   BF16X3  operand = three bf16 parts, 6 cross products, FP32 accumulation;
- *   FP16    each operand rounded to fp16 after a per-row power-of-two scale.
- * MLMD_C128 domains always use FP64. */
+ *   FP16    each operand rounded to fp16 after one power-of-two scale that
+ *           brings a normalised orbital's entries to O(1).
+ * The atom-projector products inside the time step (Eq. 3's nonlocal term)
+ * are FP32 in every mode.  MLMD_C128 domains always use FP64. */
 enum { MLMD_GEMM_FP32 = 0, MLMD_GEMM_BF16 = 1, MLMD_GEMM_BF16X2 = 2, MLMD_GEMM_BF16X3 = 3, MLMD_GEMM_FP16 = 4 };
 
 /* FULL: Taylor-4 of the whole h (v_nl inside the expansion).
