@@ -45,7 +45,7 @@ STAGE_BYTES_PER_UNIT = 16 + 3 * 24
 STAGE_TRAFFIC_BYTES_PER_LAUNCH = 683.1e6
 
 
-def _is_bench_workload(spec, args):
+def _is_bench_workload(spec):
     """The traffic figure was measured on the 48^3 x 256 domain with 64 x 4
     projectors; other sizes report none."""
     return spec.n == (48, 48, 48) and spec.n_orb == 256 and spec.n_proj == 4 and len(spec.atoms) == 64
@@ -345,7 +345,7 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_source": f"{peak_src} hbm_gbs",
                      "bytes_per_unit_step": STAGE_BYTES_PER_UNIT,
-                     "traffic": STAGE_TRAFFIC_BYTES_PER_LAUNCH if _is_bench_workload(spec, args) else None,
+                     "traffic": STAGE_TRAFFIC_BYTES_PER_LAUNCH if _is_bench_workload(spec) else None,
                      "traffic_unit": "bytes per stage launch (ncu, mean of the four stage launches of a step)",
                      "kernel_share": {"stage": st_ms / t_ms, "project": pr_ms / t_ms},
                      "launches": {"stage": st_n, "project": pr_n}},
