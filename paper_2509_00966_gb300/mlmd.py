@@ -267,6 +267,43 @@ def propagate_adjoint(h, A, ckpt_every, n_grid, dL_dV=None):
     return loss.value, dA, dL_dV
 
 
+_EXC_LOSS = None
+
+
+def _excitation_loss_fn():
+    global _EXC_LOSS
+    if _EXC_LOSS is None:
+        import torch
+
+        class ExcitationLoss(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, A, V, dom, ckpt_every):
+                Ah = A.detach().to("cpu", torch.float64).contiguous().numpy()
+                Vh = V.detach().to("cpu", torch.float64).contiguous().numpy()
+                dom.set_potential(Vh)
+                dV = torch.zeros(dom.n_grid, dtype=torch.float64, device=V.device)
+                loss, dA, dV = propagate_adjoint(dom.handle, Ah, ckpt_every, dom.n_grid, dV)
+                ctx.save_for_backward(torch.from_numpy(dA).to(A.device, A.dtype), dV.to(V.dtype))
+                return torch.tensor(loss, dtype=torch.float64, device=A.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                dA, dV = ctx.saved_tensors
+                return g.to(dA.device, dA.dtype) * dA, g.to(dV.device, dV.dtype) * dV, None, None
+
+        _EXC_LOSS = ExcitationLoss
+    return _EXC_LOSS
+
+
+def excitation_loss(dom, A, V, ckpt_every):
+    """n_exc(Psi(T)) (Sec. V.A.8) after len(A) full-scheme steps from the
+    domain's current orbitals, as a torch function of the vector-potential
+    samples A ([n_steps, 3]) and the local potential V ([N_g]); backward
+    gives mlmd_propagate_adjoint's dL/dA and dL/dV.  V becomes the domain's
+    potential and the orbitals are left at Psi(T), as the ABI call does."""
+    return _excitation_loss_fn().apply(A, V, dom, int(ckpt_every))
+
+
 def batch_create(handles):
     arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
     out = ctypes.c_void_p()
@@ -425,6 +462,9 @@ class Domain:
 
     def propagate_adjoint(self, A, ckpt_every, dL_dV=None):
         return propagate_adjoint(self.handle, A, ckpt_every, self.n_grid, dL_dV)
+
+    def excitation_loss(self, A, V, ckpt_every):
+        return excitation_loss(self, A, V, ckpt_every)
 
     @property
     def launches(self):

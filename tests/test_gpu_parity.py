@@ -234,6 +234,28 @@ def test_adjoint_against_oracle(precision):
     d.close()
 
 
+def test_adjoint_as_autograd_function():
+    """The adjoint behind torch.autograd: from the same start, backward of
+    excitation_loss leaves the direct mlmd_propagate_adjoint's dL/dV in V's
+    gradient, and the chain rule through A = s A0 gives dL/ds = sum dL/dA A0."""
+    import torch
+    spec = small_spec(precision="c128", n=(8, 9, 10), n_orb=6, steps=10, n_atoms=4)
+    d, V = gpu_domain(spec)
+    psi = orbitals(spec)
+    d.set_orbitals(to_device(psi, "c128"))
+    loss0, dA0, dV0 = d.propagate_adjoint(spec.A, ckpt_every=4)
+    d.set_orbitals(to_device(psi, "c128"))
+    s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    Vt = torch.from_numpy(np.ascontiguousarray(V)).cuda().requires_grad_(True)
+    loss = d.excitation_loss(s * torch.from_numpy(spec.A), Vt, ckpt_every=4)
+    loss.backward()
+    assert abs(loss.item() - loss0) <= 1e-12 * max(1.0, abs(loss0))
+    np.testing.assert_allclose(Vt.grad.cpu().numpy(), dV0, rtol=1e-12, atol=1e-14 * np.abs(dV0).max())
+    ds = float(np.sum(dA0 * spec.A))
+    assert abs(s.grad.item() - ds) <= 1e-10 * max(1.0, abs(ds))
+    d.close()
+
+
 def test_batch_matches_single_domains_and_oracle():
     specs = [small_spec(n=(10, 10, 10), n_orb=7, seed=1, steps=6), small_spec(n=(12, 9, 11), n_orb=16, seed=2, steps=6),
              small_spec(n=(8, 8, 12), n_orb=3, seed=3, steps=6, n_atoms=2)]
