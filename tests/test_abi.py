@@ -78,6 +78,13 @@ def test_null_arguments_rejected(lib):
     assert lib.mlmd_domain_create(None, None, None, None) == 1
     assert lib.mlmd_domain_destroy(None) == 1
     assert lib.mlmd_propagate(None, 1, None, None) == 1
+    # every entry point that takes a handle rejects a null one before touching a device
+    v = ctypes.c_double()
+    assert lib.mlmd_excitation(None, ctypes.byref(v)) == 1
+    assert lib.mlmd_occupations(None, None, ctypes.byref(v)) == 1
+    assert lib.mlmd_ks_correction(None, None) == 1
+    assert lib.mlmd_overlap(None, None) == 1
+    assert lib.mlmd_reorthonormalize(None, 0) == 1
     assert lib.mlmd_batch_create(0, None, None) == 1
     assert lib.mlmd_last_error(None) == b"null handle"
     assert lib.mlmd_launch_count(None) == 0
