@@ -88,3 +88,26 @@ def test_null_arguments_rejected(lib):
     assert lib.mlmd_batch_create(0, None, None) == 1
     assert lib.mlmd_last_error(None) == b"null handle"
     assert lib.mlmd_launch_count(None) == 0
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with libmlmd missing, the first call raises instead of
+    computing anything another way."""
+    monkeypatch.setattr(mlmd, "_lib", None)
+    monkeypatch.setattr(mlmd, "LIB_PATH", str(tmp_path / "libmlmd.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        mlmd.abi_version()
+
+
+def test_seeded_inputs_repeat():
+    """Both sides get their inputs from the seeded generators: the same
+    workload twice gives the same arrays, bit for bit."""
+    import numpy as np
+    from paper_2509_00966_gb300 import inputs
+    for name in ["c0", "c4"]:
+        a, b = inputs.config(name, n_steps=3), inputs.config(name, n_steps=3)
+        for f in ["wells", "well_depth", "atoms", "D", "A", "occ"]:
+            assert np.array_equal(getattr(a, f), getattr(b, f)), (name, f)
+    p1 = inputs.random_orbitals(500, 4, 0.1, 3)
+    assert np.array_equal(p1, inputs.random_orbitals(500, 4, 0.1, 3))
+    assert not np.array_equal(p1, inputs.random_orbitals(500, 4, 0.1, 4))
