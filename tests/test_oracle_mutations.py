@@ -28,6 +28,12 @@ MUTANTS = [
     ("minimum image without the half shift", "double k = floor(t / L[ax] + 0.5);", "double k = floor(t / L[ax]);"),
     ("current without the A rho term", "jcur[ax * ng + g] = s + A[ax] * rho[g];", "jcur[ax * ng + g] = s;"),
     ("adjoint Taylor with the forward sign", "c *= (I * dt) / (double)j;", "c *= (-I * dt) / (double)j;"),
+    ("2nd-order laplacian centre coefficient", "lap[0] = -2.0; lap[1] = 1.0;", "lap[0] = -2.1; lap[1] = 1.0;"),
+    ("4th-order laplacian inner coefficient", "lap[1] = 4.0 / 3.0", "lap[1] = 4.0 / 3.1"),
+    ("4th-order gradient inner coefficient", "grad[1] = 2.0 / 3.0", "grad[1] = 2.0 / 3.1"),
+    ("projector normalised without dV", "s *= dV;", ";"),
+    ("split step without the renormalisation", "sqrt(nrm_before[o] / nrm_after[o])", "1.0"),
+    ("overlap without dV", "S[(int64_t)n * nb + m] = dV * s;", "S[(int64_t)n * nb + m] = s;"),
     ("energy without the nonlocal part", "orc_apply_h(d, A, psi_in, work, work_proj);\n    for (int64_t g = 0; g < ng; ++g)\n        for (int o = 0; o < no; ++o) {\n            cplx c = in[g * no + o];\n            nrm",
      "orc_apply_hloc(d, A, psi_in, work);\n    for (int64_t g = 0; g < ng; ++g)\n        for (int o = 0; o < no; ++o) {\n            cplx c = in[g * no + o];\n            nrm"),
 ]
