@@ -204,6 +204,23 @@ def test_neighbor_list_brute_force_count():
     assert 0 in xs and n[0] - 1 in xs
 
 
+def test_neighbor_list_exact_tie_is_member():
+    """A point at exactly r_cut belongs to the sphere (d^2 <= r_cut^2): with
+    h = 0.5 and r_cut = 1.5 (both exact in binary) and the atom on a grid
+    point, every offset with |m|^2 = 9 -- (3,0,0) and (2,2,1) up to signs and
+    order, 30 points -- lies exactly on the sphere."""
+    n, h, rcut = (16, 16, 16), 0.5, 1.5
+    pos = np.array([[4 * h, 5 * h, 6 * h]])
+    off, idx = oracle.neighbor_lists(n, h, pos, rcut)
+    inside = sum(1 for i in range(-3, 4) for j in range(-3, 4) for k in range(-3, 4) if i * i + j * j + k * k <= 9)
+    on = sum(1 for i in range(-3, 4) for j in range(-3, 4) for k in range(-3, 4) if i * i + j * j + k * k == 9)
+    assert on == 30
+    assert off[1] - off[0] == inside
+    lst = set(idx[off[0]:off[1]].tolist())
+    assert (4 + 3) + 16 * (5 + 16 * 6) in lst                   # offset (3, 0, 0)
+    assert (4 + 2) + 16 * ((5 - 2) + 16 * (6 + 1)) in lst       # offset (2, -2, 1)
+
+
 def test_neighbor_list_translation_and_wrap():
     n, h, rcut = (16, 16, 16), 0.5, 1.6
     pos = np.array([[3.25, 4.125, 7.5]])
