@@ -127,6 +127,25 @@ def test_projector_lists_bit_exact():
         d.close()
 
 
+def test_projector_lists_exact_tie():
+    """Points exactly at r_cut belong to the sphere on both sides: h = 0.5,
+    r_cut = 1.5 and atoms on grid points make d^2 = r_cut^2 exact in binary
+    for 30 offsets per atom; the device lists equal the oracle's."""
+    from paper_2509_00966_gb300 import mlmd
+    n, h = (16, 16, 16), 0.5
+    pos = np.array([[2.0, 2.5, 3.0], [0.0, 0.0, 0.0], [7.5, 7.5, 7.5]])
+    D = np.ones((3, 4))
+    d = mlmd.Domain(n, h, 4, 4, "c128", dt=0.02)
+    d.set_projectors(pos, 4, 0.9, 1.5, D)
+    off, idx, beta = d.projector_lists()
+    V = np.zeros(int(np.prod(n)))
+    od = oracle.Domain(n, h, 4, 4, V, pos, 4, 0.9, 1.5, D)
+    np.testing.assert_array_equal(off, od.off)
+    np.testing.assert_array_equal(idx, od.idx)
+    assert all(off[a + 1] - off[a] == 123 for a in range(3))   # |m|^2 <= 9: 123 offsets
+    d.close()
+
+
 def test_projector_edge_cases():
     # an atom whose sphere holds no grid point, atoms far outside the box, 8 shapes
     spec = small_spec(n_atoms=3, n_proj=8, r_cut=1.5, precision="c128", steps=3)
