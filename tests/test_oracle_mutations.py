@@ -35,6 +35,9 @@ MUTANTS = [
     ("split step without the renormalisation", "sqrt(nrm_before[o] / nrm_after[o])", "1.0"),
     ("overlap without dV", "S[(int64_t)n * nb + m] = dV * s;", "S[(int64_t)n * nb + m] = s;"),
     ("sphere membership without the boundary", "if (d2 <= rc2) {", "if (d2 < rc2) {"),
+    ("density without the occupations", "s += f[o] * creal(conj(c) * c);", "s += creal(conj(c) * c);"),
+    ("current field with the conjugate on the gradient", "cimag(conj(in[g * no + o]) * gp[g * no + o])",
+     "cimag(in[g * no + o] * conj(gp[g * no + o]))"),
     ("energy without the nonlocal part", "orc_apply_h(d, A, psi_in, work, work_proj);\n    for (int64_t g = 0; g < ng; ++g)\n        for (int o = 0; o < no; ++o) {\n            cplx c = in[g * no + o];\n            nrm",
      "orc_apply_hloc(d, A, psi_in, work);\n    for (int64_t g = 0; g < ng; ++g)\n        for (int o = 0; o < no; ++o) {\n            cplx c = in[g * no + o];\n            nrm"),
 ]
