@@ -35,6 +35,12 @@ MUTANTS = [
     ("split step without the renormalisation", "sqrt(nrm_before[o] / nrm_after[o])", "1.0"),
     ("overlap without dV", "S[(int64_t)n * nb + m] = dV * s;", "S[(int64_t)n * nb + m] = s;"),
     ("sphere membership without the boundary", "if (d2 <= rc2) {", "if (d2 < rc2) {"),
+    ("projector Gaussian without the factor 2 in its width", "double s = exp(-d2 / (2.0 * rc * rc));",
+     "double s = exp(-d2 / (rc * rc));"),
+    ("second projector shell at r_c sqrt(2)", "double rc = set == 0 ? r_c : r_c / sqrt(2.0);",
+     "double rc = set == 0 ? r_c : r_c * sqrt(2.0);"),
+    ("p projector with the displacement reversed", "beta[q * n_proj + 4 * set + 1 + ax] = dl[ax] / rc * s;",
+     "beta[q * n_proj + 4 * set + 1 + ax] = -dl[ax] / rc * s;"),
     ("density without the occupations", "s += f[o] * creal(conj(c) * c);", "s += creal(conj(c) * c);"),
     ("current field with the conjugate on the gradient", "cimag(conj(in[g * no + o]) * gp[g * no + o])",
      "cimag(in[g * no + o] * conj(gp[g * no + o]))"),

@@ -262,6 +262,51 @@ def test_projector_trace_any_position_8_shapes():
     assert np.max(np.abs(Vnl - Vnl.T)) < 1e-14 and np.max(np.abs(Vnl.imag)) == 0.0
 
 
+def test_projector_radial_profile_ratios():
+    """The radial shape of every projector, free of its normalisation: with
+    the atom on a grid point the displacement to a point is exactly m h for
+    an integer offset m, so within one projector the ratio of two values is
+    fixed by the Gaussian width alone,
+        s(m) / s(m')     = exp(-(|m|^2 - |m'|^2) h^2 / (2 w^2)),
+        p_x(m) / p_x(m') = (m_x / m'_x) exp(-(|m|^2 - |m'|^2) h^2 / (2 w^2)),
+    with w = r_c for the first four projectors and w = r_c / sqrt(2) for the
+    second four of the 8-projector set.  The normalisation constant cancels,
+    so this pins the width, the second shell's width and the sign and axis of
+    the p factor independently of the trace and spectrum pins."""
+    n, h, r_c, r_cut = (14, 13, 12), 0.5, 0.9, 1.6
+    c = np.array([5, 6, 7])
+    pos = (c * h)[None, :].astype(np.float64)
+    off, idx = oracle.neighbor_lists(n, h, pos, r_cut)
+    beta = oracle.projector_values(n, h, pos, off, idx, 8, r_c)
+    where = {int(g): q for q, g in enumerate(idx[off[0]:off[1]])}
+
+    def val(m, i):
+        x, y, z = (c + np.array(m)) % np.array(n)
+        return beta[where[int(x + n[0] * (y + n[1] * z))], i]
+
+    shells = [(1, 0, 0), (1, 1, 0), (2, 0, 0), (1, 1, 1), (2, 1, 1), (3, 0, 0)]
+    for st, w in ((0, r_c), (4, r_c / math.sqrt(2.0))):
+        for a in range(len(shells)):
+            for b in range(a + 1, len(shells)):
+                ma, mb = np.array(shells[a]), np.array(shells[b])
+                ratio = math.exp(-(ma @ ma - mb @ mb) * h * h / (2.0 * w * w))
+                assert abs(val(ma, st) / val(mb, st) - ratio) < 1e-12 * ratio
+                # p_x, p_y, p_z: the same Gaussian times the displacement along its own axis
+                for ax in range(3):
+                    if ma[ax] != 0 and mb[ax] != 0:
+                        r = ratio * ma[ax] / mb[ax]
+                        assert abs(val(ma, st + 1 + ax) / val(mb, st + 1 + ax) - r) < 1e-12 * abs(r)
+        for ax in range(3):
+            e = np.zeros(3, int)
+            e[ax] = 1
+            assert val(e, st + 1 + ax) > 0.0                       # delta = r - R: positive on the + side
+            np.testing.assert_allclose(val(-e, st + 1 + ax), -val(e, st + 1 + ax), rtol=1e-14)
+            assert val(np.roll(e, 1), st + 1 + ax) == 0.0           # no displacement along the axis: zero
+    # the two shells really differ in width: s(1,0,0) / s(2,0,0) is e^{3 h^2 / (2 r_c^2)} and e^{3 h^2 / r_c^2}
+    assert abs(val((1, 0, 0), 0) / val((2, 0, 0), 0) - math.exp(3 * h * h / (2 * r_c * r_c))) < 1e-12 * 2
+    assert abs(val((1, 0, 0), 4) / val((2, 0, 0), 4) - math.exp(3 * h * h / (r_c * r_c))) < 1e-12 * 3
+
+
 # ---------------------------------------------------------------------------
 # observables
 # ---------------------------------------------------------------------------
