@@ -252,9 +252,11 @@ MLMD_API mlmd_status mlmd_batch_propagate(mlmd_batch_t batch, int32_t n_steps, c
  * holds until exit, so n_orb may be at most MLMD_OVERLAP_NOALLOC_MAX_ORB
  * (larger values return MLMD_ERR_INVALID).  All calls share that array:
  * calls whose kernels overlap on the GPU (e.g. on two streams) race and give
- * wrong results.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. */
+ * wrong results.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, a host-side lookup that allocates nothing) with the
+ * current device, so a call after a device reset finds the array where the
+ * reloaded library put it; the first call on a device may load the library's
+ * device code, so make that first call before any stream capture. */
 #define MLMD_OVERLAP_NOALLOC_MAX_ORB 512
 MLMD_API mlmd_status mlmd_overlap_noalloc(int32_t precision, int64_t n_grid, int32_t n_orb, const void* X,
                                           const void* Y, double scale, double* S, void* stream);

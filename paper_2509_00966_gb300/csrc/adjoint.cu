@@ -113,6 +113,7 @@ extern "C" mlmd_status mlmd_propagate_adjoint(mlmd_domain_t dom, int32_t n_steps
         std::vector<double> hC((size_t)2 * no * no);
         MLMD_CUDA(cudaMemcpyAsync(hC.data(), C, sizeof(double) * hC.size(), cudaMemcpyDeviceToHost, d->stream));
         MLMD_CUDA(cudaStreamSynchronize(d->stream));
+        check_err_flag(*d);       // a forward stage that gave up a wait leaves psi(T) and the loss wrong
         double s2 = 0.0;
         for (double v : hC) s2 += v * v;
         *loss = 2.0 * ((double)no - s2);
@@ -180,6 +181,7 @@ extern "C" mlmd_status mlmd_propagate_adjoint(mlmd_domain_t dom, int32_t n_steps
                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d->stream));
         MLMD_CUDA(cudaStreamSynchronize(d->stream));
         MLMD_CUDA(cudaGetLastError());
+        check_err_flag(*d);       // recompute and backward sweep launch the same bounded-wait kernels
         for (int k = 0; k < n_steps; ++k)
             for (int a = 0; a < 3; ++a) {
                 dL_dA[3 * k + a] = hg[4 * k + a] + A[3 * k + a] * hg[4 * k + 3];
@@ -189,7 +191,8 @@ extern "C" mlmd_status mlmd_propagate_adjoint(mlmd_domain_t dom, int32_t n_steps
         return MLMD_OK;
     } catch (const Error& e) {
         d->err = e.msg;
-        if (e.status == MLMD_ERR_CUDA || e.status == MLMD_ERR_NUMERIC) d->latched = e.status;
+        if (e.status == MLMD_ERR_CUDA || e.status == MLMD_ERR_NUMERIC || e.status == MLMD_ERR_TIMEOUT)
+            d->latched = e.status;
         return e.status;
     } catch (...) {
         d->err = "unexpected failure";

@@ -110,6 +110,15 @@ void step_full(Domain& d, const double* Ak, double* obs_row) {
     d.pa_psi = chain;
 }
 
+// Raise MLMD_ERR_TIMEOUT if a kernel's bounded device-side wait expired:
+// reads the domain's error word in stream order and synchronises the stream.
+void check_err_flag(Domain& d) {
+    int h = 0;
+    MLMD_CUDA(cudaMemcpyAsync(&h, d.err_flag, sizeof(int), cudaMemcpyDeviceToHost, d.stream));
+    MLMD_CUDA(cudaStreamSynchronize(d.stream));
+    MLMD_REQUIRE(h == 0, MLMD_ERR_TIMEOUT, "a device-side wait timed out");
+}
+
 // ---------------------------------------------------------------------------
 // kernel timing
 // ---------------------------------------------------------------------------
@@ -304,14 +313,6 @@ void upload_occupations(Domain& d, const std::vector<double>& f) {
         MLMD_CUDA(cudaMemcpyAsync(d.fR, f.data(), sizeof(double) * d.ld, cudaMemcpyHostToDevice, d.stream));
         MLMD_CUDA(cudaStreamSynchronize(d.stream));
     }
-}
-
-// Raise MLMD_ERR_TIMEOUT if a kernel's bounded device-side wait expired
-// (the caller has synchronised the domain's stream).
-void check_err_flag(Domain& d) {
-    int h = 0;
-    MLMD_CUDA(cudaMemcpy(&h, d.err_flag, sizeof(int), cudaMemcpyDeviceToHost));
-    MLMD_REQUIRE(h == 0, MLMD_ERR_TIMEOUT, "a device-side wait timed out");
 }
 
 void check_desc(const mlmd_domain_desc* s) {

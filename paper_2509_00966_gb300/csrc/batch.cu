@@ -186,6 +186,12 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
                                       cudaMemcpyDeviceToHost, st));
         MLMD_CUDA(cudaStreamSynchronize(st));
         MLMD_CUDA(cudaGetLastError());
+        // a stage or projection kernel inside the graph that gave up a bounded
+        // wait has left its domain's orbitals wrong: report it per domain
+        for (auto* d : b->doms) {
+            d->stream = st;
+            check_err_flag(*d);
+        }
         (void)cudaGraphExecDestroy(exec);
         (void)cudaGraphDestroy(graph);
         exec = nullptr;
@@ -208,7 +214,8 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         if (exec) (void)cudaGraphExecDestroy(exec);
         if (graph) (void)cudaGraphDestroy(graph);
         d0.err = e.msg;
-        if (e.status == MLMD_ERR_CUDA) for (auto* d : b->doms) d->latched = MLMD_ERR_CUDA;
+        if (e.status == MLMD_ERR_CUDA || e.status == MLMD_ERR_TIMEOUT)
+            for (auto* d : b->doms) d->latched = e.status;
         return e.status;
     } catch (...) {
         return MLMD_ERR_STATE;

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(192, 1)
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], filled[2], drained[2], done;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_sh;
+    __shared__ int consumed_sh;          // steps whose copies the MMA thread has seen land
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int ta, tb;
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         mbar_init(&done, 1);
         abort_sh = 0;
+        consumed_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -149,6 +151,7 @@ __global__ void __launch_bounds__(192, 1)
     bool drained_all = false;            // drain warps: every run is in the sums
     float sum[BN];                       // drain warps: running sums of one tile row
 
+    int issued = 0;                      // producer: steps whose copies were issued
     if (tid == 0) {                     // producer
         for (int i = 0; i < nsteps && !abort_sh; ++i) {
             const int st = i % STAGES;
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(192, 1)
                 bulk_load(Bs + p * kTileBytes, pb + (((int64_t)p * nmt + tb) * nks + ks) * kTileBytes, kTileBytes,
                           &full[st]);
             }
+            issued = i + 1;
         }
     } else if (tid == 32) {             // MMA issuer
         for (int i = 0; i < nsteps; ++i) {
@@ -182,6 +186,7 @@ __global__ void __launch_bounds__(192, 1)
                 abort_sh = 1;
                 break;
             }
+            consumed_sh = i + 1;
             tc_fence_after();
             const uint32_t As = smem_u32(smem + st * STAGE_BYTES);
             const uint32_t Bs = As + NPART * kTileBytes;
@@ -190,8 +195,8 @@ __global__ void __launch_bounds__(192, 1)
             for (int p = 0; p < NPROD; ++p)
 #pragma unroll
                 for (int kk = 0; kk < KSTEPS_PER_MMA; ++kk) {
-                    const uint64_t ad = smem_desc(As + prod_a(p) * kTileBytes + kk * 256, 128, 1024);
-                    const uint64_t bd = smem_desc(Bs + prod_b(p) * kTileBytes + kk * 256, 128, 1024);
+                    const uint64_t ad = smem_desc(As + prod_a(p, NPROD) * kTileBytes + kk * 256, 128, 1024);
+                    const uint64_t bd = smem_desc(Bs + prod_b(p, NPROD) * kTileBytes + kk * 256, 128, 1024);
                     mma_f16(acc, ad, bd, IDESC, (first && p == 0 && kk == 0) ? 0u : 1u);
                 }
             mma_commit(&empty[st]);
@@ -231,8 +236,10 @@ __global__ void __launch_bounds__(192, 1)
     if (abort_sh) {
         if (tid == 0) {
             atomicExch(err, 1);
-            // let bulk copies still in flight land (bounded)
-            for (int st = 0; st < STAGES; ++st) (void)mbar_wait_bounded(&full[st], 0);
+            // let the bulk copies still in flight land (bounded): every step
+            // issued but not seen by the MMA thread, on its own phase
+            for (int i = consumed_sh; i < issued; ++i)
+                (void)mbar_wait_bounded(&full[i % STAGES], (uint32_t)((i / STAGES) & 1));
         }
     } else if (warp >= 2 && drained_all && nsteps > 0) {
         // row of G held by this lane; rows 2a and 2a+1 sit in neighbouring lanes

@@ -147,7 +147,7 @@ template <typename R> struct TGeo {
 };
 
 // Shared-memory slot of w: centre [TY][TX][VP], xm/xp [TY][2][VP], ym/yp
-// [2][TX][VP] (16-byte vectors).  psi's centre tiles have a ring of their own.
+// [2][TX][VP] (16-byte vectors).
 template <int VP> struct Slot {
     static constexpr int C = 0;
     static constexpr int XM = C + TY * TX * VP;
@@ -156,10 +156,10 @@ template <int VP> struct Slot {
     static constexpr int YP = YM + 2 * TX * VP;
     static constexpr int N = YP + 2 * TX * VP;    // vectors per slot
     static constexpr uint32_t BYTES = N * 16;
-    static constexpr int PN = TY * TX * VP;       // vectors of a psi tile
-    static constexpr uint32_t PSI_BYTES = PN * 16;
 };
-constexpr int PSL = 3;                            // psi ring slots
+// Scatter entry blocks have a ring of their own: the block of computed plane
+// j is brought two planes ahead of its use into slot j % ESL.
+constexpr int ESL = 3;
 
 // Vector (x+dx, y+dy) of the plane in slot s, one of dx, dy zero, |d| <= 2.
 template <int VP>
@@ -255,7 +255,7 @@ __device__ __forceinline__ float2 swp(float2 v) { return make_float2(v.y, v.x); 
 template <typename R, int ORDER, int VP, int NP, int NSLOT, int TPP, bool OBS>
 __global__ void __launch_bounds__(64 * TPP, 2)
     k_stage_tma(const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_x,
-                const __grid_constant__ CUtensorMap tm_y, const __grid_constant__ CUtensorMap tm_p, int psi_mode,
+                const __grid_constant__ CUtensorMap tm_y, const R* __restrict__ psi_g, int psi_mode,
                 TGeo<R> G, R* out,
                 const R* __restrict__ V, const R* __restrict__ f, const double* __restrict__ Ak, TNl<R> N,
                 R gre, R gim, double* __restrict__ obs, int* err) {
@@ -269,11 +269,10 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     // TMA destinations on a 1024-byte boundary (the launch adds 1024 bytes of
     // slack): the swizzle pattern is a function of the address bits
     float4* ring = reinterpret_cast<float4*>(smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u));
-    float4* sPsi = ring + NSLOT * Slot<VP>::N;      // [PSL][TY][TX][VP] psi tiles
-    float4* sP = sPsi + PSL * Slot<VP>::PN;         // [maxs][NP][VP] staged <b|w>
-    unsigned char* sE = reinterpret_cast<unsigned char*>(sP + N.maxs * NPV * VP);   // [NSLOT][scap] entry blocks
+    float4* sP = ring + NSLOT * Slot<VP>::N;        // [maxs][NP][VP] staged <b|w>
+    unsigned char* sE = reinterpret_cast<unsigned char*>(sP + N.maxs * NPV * VP);   // [ESL][scap] entry blocks
     __shared__ __align__(8) uint64_t bars[NSLOT];
-    __shared__ __align__(8) uint64_t pbars[PSL];
+    __shared__ __align__(8) uint64_t ebars[ESL];
     __shared__ int64_t soff[17];                    // entry-block offsets of the column's planes (zc <= 16)
     __shared__ R sA[4];
     __shared__ int abort_sh;
@@ -291,7 +290,8 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     const int nplanes = nzc + 4;                    // planes z0-2 .. z0+nzc+1
     const int c0 = chunk * OCR;                     // first real of the chunk within a row
     // psi_mode 0: out = gamma h w; 1: psi is w itself (its centre tile is in
-    // the ring already); 2: psi's centre tile comes with each plane
+    // the ring already); 2: each thread reads its own vectors of psi from
+    // global memory, one plane ahead (no shared-memory round trip)
     const bool has_psi = psi_mode != 0;
     // complex64 launches take the packed path: h w as sum_n c_n w_n with the
     // complex coefficient c_n = k_n - i a_n of each stencil neighbour (k from
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
-        for (int s = 0; s < PSL; ++s) mbar_init(&pbars[s], 1);
+        for (int s = 0; s < ESL; ++s) mbar_init(&ebars[s], 1);
         abort_sh = 0;
         fence_proxy_async();
     }
@@ -327,16 +327,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         const int zz = ((z0 - 2 + p) % G.nz + G.nz) % G.nz;
         float4* d = ring + s * Slot<VP>::N;
         uint64_t* b = &bars[s];
-        // the scatter entries of computed plane p - 2 travel with w plane p
-        const int j = p - 2;
-        uint32_t eb = 0;
-        int64_t eo = 0;
-        if (NP > 0 && j >= 0 && j < nzc) {
-            eo = soff[j];
-            eb = (uint32_t)(soff[j + 1] - eo);
-        }
-        mbar_expect_tx(b, Slot<VP>::BYTES + eb);
-        if (eb) bulk_g2s(sE + (size_t)s * N.scap, N.sblk + eo, eb, b);
+        mbar_expect_tx(b, Slot<VP>::BYTES);
         tma_load_4d(d + Slot<VP>::C, &tm_c, c0, x0, y0, zz, b);
         tma_load_4d(d + Slot<VP>::XM, &tm_x, c0, (x0 - 2 + G.nx) % G.nx, y0, zz, b);
         tma_load_4d(d + Slot<VP>::XP, &tm_x, c0, (x0 + TX) % G.nx, y0, zz, b);
@@ -344,14 +335,16 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         tma_load_4d(d + Slot<VP>::YP, &tm_y, c0, x0, (y0 + TY) % G.ny, zz, b);
     };
     auto wait_plane = [&](int p) -> bool { return mbar_wait_bounded(&bars[p % NSLOT], (uint32_t)((p / NSLOT) & 1)); };
-    // psi tile of computed plane j (z = z0 + j) into psi slot j % PSL
-    int issued_p = 0, waited_p = 0;                 // meaningful in thread 0
-    auto issue_psi = [&](int j) {
-        if (psi_mode != 2 || j >= nzc) return;
-        uint64_t* b = &pbars[j % PSL];
-        mbar_expect_tx(b, Slot<VP>::PSI_BYTES);
-        tma_load_4d(sPsi + (j % PSL) * Slot<VP>::PN, &tm_p, c0, x0, y0, z0 + j, b);
-        issued_p = j + 1;
+    // scatter entry block of computed plane j (z = z0 + j) into entry slot j % ESL
+    int issued_e = 0, waited_e = 0;                 // meaningful in thread 0
+    auto issue_e = [&](int j) {
+        if (NP == 0 || j >= nzc) return;
+        const int64_t eo = soff[j];
+        const uint32_t eb = (uint32_t)(soff[j + 1] - eo);     // >= the 272-byte header
+        uint64_t* b = &ebars[j % ESL];
+        mbar_expect_tx(b, eb);
+        bulk_g2s(sE + (size_t)(j % ESL) * N.scap, N.sblk + eo, eb, b);
+        issued_e = j + 1;
     };
 
     // shared-memory offsets (16-byte vectors) of this thread's first vector and
@@ -362,7 +355,6 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     static_assert(NVT == 1 || NVT == 2, "one or two vectors per thread");
     const int vb = jv * NVT;
     const int offC = swz<VP>(Slot<VP>::C + (ly * TX + lx) * VP, vb);
-    const int offPs = swz<VP>(pt * VP, vb);        // within a psi tile
     int offN[8];
     {
         const int dx[8] = {1, -1, 0, 0, 2, -2, 0, 0}, dy[8] = {0, 0, 1, -1, 0, 0, 2, -2};
@@ -374,7 +366,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     if (tid == 0) {
         for (int p = 0; p < NSLOT && p < nplanes; ++p) issue(p);
         issued = min(NSLOT, nplanes);
-        for (int j = 0; j < PSL - 1; ++j) issue_psi(j);
+        for (int j = 0; j < ESL - 1; ++j) issue_e(j);
     }
     // register window of the thread's vectors: q[k][0..4] = planes z-2 .. z+2
     float4 q[NVT][5];
@@ -414,11 +406,20 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     int64_t g = (x0 + lx) + (int64_t)G.nx * (y0 + ly) + plane_stride * z0;
     const int64_t row = 2 * (int64_t)G.ld;
     R vnext = nzc > 0 ? V[g] : (R)0;       // V one plane ahead
+    // this thread's vectors of psi (psi_mode 2) come straight from global
+    // memory: issued at the top of the plane, used after the stencil and the
+    // scatter, whose shared-memory work covers the load latency
+    const int64_t row_v = row * (int64_t)sizeof(R) / 16;      // 16-byte vectors per row
+    const float4* psi_v = psi_mode == 2 ? reinterpret_cast<const float4*>(psi_g + c0) + vb : nullptr;
     for (int i = 0; i < nzc && !aborted0; ++i, g += plane_stride) {
         // per-point global loads first, so that they overlap the plane wait
         // and the shared-memory stencil
         const R vv = vnext;
         if (i + 1 < nzc) vnext = V[g + plane_stride];
+        float4 ps_cur[NVT];
+#pragma unroll
+        for (int k = 0; k < NVT; ++k)
+            ps_cur[k] = psi_mode == 2 ? __ldg(psi_v + g * row_v + k) : make_float4(0.f, 0.f, 0.f, 0.f);
         // plane z+2 (p = i+4) must have landed
         ok = wait_plane(i + 4);
         if (!ok) abort_sh = 1;
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 issue(issued);
                 ++issued;
             }
-            issue_psi(i + PSL - 1);         // into the psi slot of plane z-1
+            issue_e(i + ESL - 1);           // into the entry slot of plane z-1
         }
         const float4* sc = ring + ((i + 2) % NSLOT) * Slot<VP>::N;    // plane z
         const float4* s4 = ring + ((i + 4) % NSLOT) * Slot<VP>::N;    // plane z+2
@@ -555,8 +556,16 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             }
         }
         }
-        if (NP > 0) {           // scatter-back: sum_(a,i) b_ai(r) D_ai <b_ai|w>
-            const unsigned char* eb = sE + (size_t)((i + 2) % NSLOT) * N.scap;
+        // the entry block of this plane must have landed; on a timeout the
+        // scatter is skipped (the CTA aborts) rather than read a stale block
+        bool e_ok = true;
+        if (NP > 0) {
+            e_ok = mbar_wait_bounded(&ebars[i % ESL], (uint32_t)((i / ESL) & 1));
+            if (!e_ok) abort_sh = 1;
+            else if (tid == 0) waited_e = i + 1;
+        }
+        if (NP > 0 && e_ok) {   // scatter-back: sum_(a,i) b_ai(r) D_ai <b_ai|w>
+            const unsigned char* eb = sE + (size_t)(i % ESL) * N.scap;
             const int32_t* hdr = reinterpret_cast<const int32_t*>(eb);
             const int32_t* eslot = hdr + 68;
             const R* ebd = reinterpret_cast<const R*>(eb + 272 + 4 * hdr[66]);
@@ -587,15 +596,11 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 }
             }
         }
-        if (psi_mode == 2) {                // psi tile of this plane (issued two planes ago)
-            if (!mbar_wait_bounded(&pbars[i % PSL], (uint32_t)((i / PSL) & 1))) abort_sh = 1;
-            if (tid == 0) waited_p = i + 1;
-        }
 #pragma unroll
         for (int k = 0; k < NVT; ++k) {
             if constexpr (FAST) {
                 const float4 ps = psi_mode == 1 ? q[k][2]
-                                  : psi_mode == 2 ? sPsi[(i % PSL) * Slot<VP>::PN + (offPs ^ k)]
+                                  : psi_mode == 2 ? ps_cur[k]
                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                 // out = psi + gamma h w, gamma = gre + i gim
                 const float2 gr2 = f2s((float)gre), gi2 = make_float2(-(float)gim, (float)gim);
@@ -623,7 +628,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             if (has_psi) {
                 Cv<R> ps;
                 if (psi_mode == 1) unpack(q[k][2], ps);
-                else unpack(sPsi[(i % PSL) * Slot<VP>::PN + (offPs ^ k)], ps);
+                else unpack(ps_cur[k], ps);
 #pragma unroll
                 for (int e = 0; e < NC; ++e) {
                     o.re[e] = ps.re[e] + gre * hw[k].re[e] - gim * hw[k].im[e];
@@ -660,8 +665,8 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             atomicExch(err, 1);
             // let the copies still in flight land before the CTA's shared memory goes away
             for (int p = waited; p < issued; ++p) (void)wait_plane(p);
-            for (int j = waited_p; j < issued_p; ++j)
-                (void)mbar_wait_bounded(&pbars[j % PSL], (uint32_t)((j / PSL) & 1));
+            for (int j = waited_e; j < issued_e; ++j)
+                (void)mbar_wait_bounded(&ebars[j % ESL], (uint32_t)((j / ESL) & 1));
         }
     }
     if constexpr (OBS) {
@@ -811,8 +816,8 @@ constexpr size_t kTwoCtaSmem = 113 * 1024;
 template <typename R, int VP, int NP>
 size_t smem_bytes(int maxs, int nslot, int scap) {
     const int npv = NP > 0 ? NP : 1;
-    size_t b = (size_t)nslot * Slot<VP>::N * 16 + (size_t)PSL * Slot<VP>::PSI_BYTES;
-    if (NP > 0) b += (size_t)maxs * npv * VP * 16 + (size_t)nslot * scap;
+    size_t b = (size_t)nslot * Slot<VP>::N * 16;
+    if (NP > 0) b += (size_t)maxs * npv * VP * 16 + (size_t)ESL * scap;
     return b + 1024;
 }
 
@@ -864,8 +869,7 @@ void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool
     {
         ProfScope ps(d.prof, MLMD_KERNEL_STAGE, d.stream);
         const int psi_mode = a.psi == nullptr ? 0 : (a.psi == a.w ? 1 : 2);
-        const CUtensorMap tm_p = psi_mode == 2 ? maps_for(d, a.psi).centre : m.centre;
-        kern<<<grid, 64 * tpp, smem, d.stream>>>(m.centre, m.xslab, m.yslab, tm_p, psi_mode, G,
+        kern<<<grid, 64 * tpp, smem, d.stream>>>(m.centre, m.xslab, m.yslab, static_cast<const R*>(a.psi), psi_mode, G,
                                            static_cast<R*>(a.out), static_cast<const R*>(d.V),
                                            static_cast<const R*>(d.fR), a.A, N, (R)a.gamma_re, (R)a.gamma_im, a.obs,
                                            d.err_flag);

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(128, 1)
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_sh;
+    __shared__ int consumed_sh;          // steps whose copies the MMA thread has seen land
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int jt = blockIdx.x, gt = blockIdx.y;
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(128, 1)
         }
         mbar_init(&done, 1);
         abort_sh = 0;
+        consumed_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t tmem = tmem_base;
     constexpr uint32_t IDESC = instr_desc(MODE == MLMD_GEMM_FP16 ? 0u : 1u);
 
+    int issued = 0;                      // producer: steps whose copies were issued
     if (tid == 0) {                     // producer
         for (int i = 0; i < nkt && !abort_sh; ++i) {
             const int st = i % STAGES;
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(128, 1)
                 bulk_load(Bs + p * kTileBytes, pb + (((int64_t)p * njt + jt) * nkt + i) * kTileBytes, kTileBytes,
                           &full[st]);
             }
+            issued = i + 1;
         }
     } else if (tid == 32) {             // MMA issuer
         for (int i = 0; i < nkt; ++i) {
@@ -204,6 +208,7 @@ __global__ void __launch_bounds__(128, 1)
                 abort_sh = 1;
                 break;
             }
+            consumed_sh = i + 1;
             tc_fence_after();
             const uint32_t As = smem_u32(smem + st * STAGE_BYTES);
             const uint32_t Bs = As + NPART * kTileBytes;
@@ -211,8 +216,8 @@ __global__ void __launch_bounds__(128, 1)
             for (int p = 0; p < NPROD; ++p)
 #pragma unroll
                 for (int kk = 0; kk < KSTEPS_PER_MMA; ++kk) {
-                    const uint64_t ad = smem_desc(As + prod_a(p) * kTileBytes + kk * 256, 128, 1024);
-                    const uint64_t bd = smem_desc(Bs + prod_b(p) * kTileBytes + kk * 256, 128, 1024);
+                    const uint64_t ad = smem_desc(As + prod_a(p, NPROD) * kTileBytes + kk * 256, 128, 1024);
+                    const uint64_t bd = smem_desc(Bs + prod_b(p, NPROD) * kTileBytes + kk * 256, 128, 1024);
                     mma_f16(tmem, ad, bd, IDESC, (i > 0 || p > 0 || kk > 0) ? 1u : 0u);
                 }
             mma_commit(&empty[st]);
@@ -220,14 +225,19 @@ __global__ void __launch_bounds__(128, 1)
         mma_commit(&done);
     }
     __syncthreads();
-    if (!abort_sh && nkt > 0 && !mbar_wait_bounded(&done, 0)) abort_sh = 1;
+    // the MMA thread commits `done` after its loop in every case, so the MMAs
+    // it issued have finished reading shared memory and writing TMEM once it fires
+    if (nkt > 0 && !mbar_wait_bounded(&done, 0)) abort_sh = 1;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (abort_sh) {
         if (tid == 0) {
             atomicExch(err, 1);
-            for (int st = 0; st < STAGES; ++st) (void)mbar_wait_bounded(&full[st], 0);
+            // let the bulk copies still in flight land (bounded): every step
+            // issued but not seen by the MMA thread, on its own phase
+            for (int i = consumed_sh; i < issued; ++i)
+                (void)mbar_wait_bounded(&full[i % STAGES], (uint32_t)((i / STAGES) & 1));
         }
     } else {
         const float unscale = (MODE == MLMD_GEMM_FP16) ? xunscale / r_scale(maxbits) : 1.f;

@@ -262,6 +262,10 @@ void lowdin_inverse_sqrt(Domain& d, double* S, double* Minv, double* work, int* 
 // Allocates nothing, so it can be captured into a CUDA graph.
 void step_full(Domain& d, const double* Ak, double* obs_row);
 
+// Raise MLMD_ERR_TIMEOUT if a kernel of the domain gave up a bounded
+// device-side wait (reads the error word in stream order; synchronises).
+void check_err_flag(Domain& d);
+
 // final reduce of per-block partials (fixed order, FP64)
 void launch_reduce_partials(Domain& d, const double* part, int nblk, int width, double* out);
 

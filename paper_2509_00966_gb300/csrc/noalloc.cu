@@ -28,20 +28,26 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_overlap_scratch[kScratchBytes];
 
 std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
 
 // The device address of the scratch array on the current device.  In host
 // code the array's name is only a host-side stand-in, so the address is
-// looked up once per device with that device current.
-cudaError_t scratch_address(int dev, void** out) {
+// looked up with the device current.  The lookup is host-side and allocates
+// nothing; it is repeated on every call rather than cached, so that a call
+// after the caller reset the device (which reloads the module and may move
+// the array) still gets the array's current address.
+cudaError_t scratch_address(void** out) { return cudaGetSymbolAddress(out, g_overlap_scratch); }
+
+// Streaming multiprocessors of a device (queried once per device).
+cudaError_t sm_count(int dev, int* out) {
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_overlap_scratch);
+    if (g_sm_count[dev] <= 0) {
+        int n = 0;
+        const cudaError_t e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        g_sm_count[dev] = n > 0 ? n : 1;
     }
-    *out = g_scratch_addr[dev];
+    *out = g_sm_count[dev];
     return cudaSuccess;
 }
 
@@ -125,10 +131,12 @@ extern "C" mlmd_status mlmd_overlap_noalloc(int32_t precision, int64_t n_grid, i
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MLMD_ERR_CUDA;
     void* scratch = nullptr;
-    if (scratch_address(dev, &scratch) != cudaSuccess) return MLMD_ERR_CUDA;
-    // split the grid points so that the launch fills the GPU, within the scratch
+    int sms = 0;
+    if (scratch_address(&scratch) != cudaSuccess || sm_count(dev, &sms) != cudaSuccess) return MLMD_ERR_CUDA;
+    // split the grid points so that the launch fills the GPU (about eight
+    // blocks per SM), within the scratch
     const int tiles = (n_orb + 31) / 32;
-    int64_t nsplit = (152 * 8) / ((int64_t)tiles * tiles) + 1;
+    int64_t nsplit = ((int64_t)sms * 8) / ((int64_t)tiles * tiles) + 1;
     nsplit = std::min<int64_t>(nsplit, (n_grid + 255) / 256);
     nsplit = std::min<int64_t>(nsplit, (int64_t)(kScratchBytes / per_split));
     nsplit = std::max<int64_t>(nsplit, 1);

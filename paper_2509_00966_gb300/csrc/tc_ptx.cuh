@@ -112,8 +112,16 @@ template <> struct Split<MLMD_GEMM_BF16X2> { static constexpr int NPART = 2, NPR
 template <> struct Split<MLMD_GEMM_BF16X3> { static constexpr int NPART = 3, NPROD = 6; };
 template <> struct Split<MLMD_GEMM_FP16> { static constexpr int NPART = 1, NPROD = 1; };
 
-__host__ __device__ constexpr int prod_a(int p) { return p == 0 ? 0 : p == 1 ? 0 : p == 2 ? 1 : p == 3 ? 0 : p == 4 ? 1 : 2; }
-__host__ __device__ constexpr int prod_b(int p) { return p == 0 ? 0 : p == 1 ? 1 : p == 2 ? 0 : p == 3 ? 2 : p == 4 ? 1 : 0; }
+// Split products (i, j) by size, largest first: (0,0), (0,1), (1,0), (0,2),
+// (1,1), (2,0); a mode with NPROD products uses the first NPROD.
+__host__ __device__ constexpr int size_rank_a(int q) { return q == 0 ? 0 : q == 1 ? 0 : q == 2 ? 1 : q == 3 ? 0 : q == 4 ? 1 : 2; }
+__host__ __device__ constexpr int size_rank_b(int q) { return q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 0 : q == 3 ? 2 : q == 4 ? 1 : 0; }
+// The p-th product issued into an accumulator, smallest first: the FP32
+// accumulation in tensor memory rounds towards zero, so adding the small
+// correction products to a still-small accumulator and the leading product
+// x0 y0 last keeps the truncation relative to the final sum to a few ulps.
+__host__ __device__ constexpr int prod_a(int p, int nprod) { return size_rank_a(nprod - 1 - p); }
+__host__ __device__ constexpr int prod_b(int p, int nprod) { return size_rank_b(nprod - 1 - p); }
 
 template <int MODE>
 static __device__ __forceinline__ void split_value(float x, float fscale, uint16_t (&part)[3]) {
