@@ -92,6 +92,9 @@ def _args():
     p.add_argument("--stage-case", nargs=4, metavar=("CFG", "N_ORB", "QD_STEPS", "REPS"),
                    help="run only stage launches of workload CFG (c1 or c2) on N_ORB orbitals, REPS propagate "
                         "calls of QD_STEPS steps (a small case for ncu captures)")
+    p.add_argument("--nl-case", nargs=4, metavar=("N", "N_ORB", "QD_STEPS", "REPS"),
+                   help="one domain of the batched workload's kind (N^3 grid, h = 0.35, round(N^3/64) atoms x 4 "
+                        "projectors): REPS propagate calls of QD_STEPS steps; per-kernel times")
     return p.parse_args()
 
 
@@ -587,6 +590,35 @@ def run_c3(args, peaks, want_cpu):
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
     launches = sum(dd.launches for dd in doms) - l0
+    # per-kernel times: one Taylor step of every domain outside the graph
+    # with per-launch CUDA events (the graph carries no timing events)
+    kinds = ("stage", "scatter", "project")
+    ktot = {k: 0.0 for k in kinds}
+    kcnt = {k: 0 for k in kinds}
+    n_list = 0
+    for dd, sp in zip(doms, specs):
+        mlmd.profile_enable(dd.handle, True)
+        dd.propagate(sp.A[:1], obs=True)
+        for k in kinds:
+            t, c = mlmd.profile_read(dd.handle, k)
+            ktot[k] += t
+            kcnt[k] += c
+        mlmd.profile_enable(dd.handle, False)
+        n_list += dd.projector_list_length() * sp.n_orb
+    # algorithmic nonlocal work of a Taylor step: per stage one projection and
+    # one scatter, 4 real flops per (list entry, projector, orbital)
+    nl_flops = 4 * 2 * 4 * 4.0 * n_list
+    nl_ms = ktot["scatter"] + ktot["project"]
+    nl_tf = nl_flops / (nl_ms * 1e-3) / 1e12 if nl_ms > 0 else None
+    roof = {"bound": "tensor", "kernel": "k_nl_scatter_tc + k_nl_project_tc (BF16x3 brick GEMMs on tcgen05)",
+            "achieved": nl_tf, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+            "frac": (nl_tf / peaks["bf16_tflops_sustained"]) if nl_tf else None,
+            "peak_source": f"{peaks['src']} bf16_tflops_sustained",
+            "algorithmic_flops_per_step": nl_flops,
+            "note": "achieved counts only the algorithmic (list-entry) nonlocal flops, not the six split products "
+                    "nor the zeros of the dense brick tiles",
+            "traffic": None,
+            "kernel_ms_per_step": {k: ktot[k] for k in kinds}, "launches_per_step": kcnt}
     # end to end: every domain's orbitals from pinned host memory, one batched
     # step, every domain's orbitals back
     pin_in = [dd.get_orbitals(device=False).pin_memory() for dd in doms]
@@ -613,6 +645,7 @@ def run_c3(args, peaks, want_cpu):
             "value": units * args.c3_steps / (t_ms * 1e-3), "unit": UNIT, "steps": args.c3_steps,
             "ms_per_step": t_ms / args.c3_steps, "units_per_step": units, "electrons": electrons,
             "t2s_s_per_electron_step": (t_ms * 1e-3) / (args.c3_steps * electrons),
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": units / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(units * 8 + len(specs) * 3 * 8),
@@ -684,6 +717,46 @@ def run_stage_case(args):
     print(json.dumps({"case": f"{cfg} on {no} orbitals", "stage_us_per_launch": 1e3 * st / max(n, 1),
                       "project_us_per_launch": 1e3 * pr / max(npj, 1), "stage_launches": n,
                       "stage_src_sha16": _sha16(STAGE_SRC)}), flush=True)
+    d.close()
+
+
+def run_nl_case(args):
+    """One c3-kind domain (dense projector spheres, tensor-core nonlocal
+    path): per-kernel mean launch times of the stage, scatter and projection
+    kernels, and the nonlocal algorithmic FLOP rate."""
+    import torch
+    from paper_2509_00966_gb300 import build, inputs, mlmd
+    build.build()
+    torch.cuda.set_device(0)
+    n, no, qd, reps = (int(v) for v in args.nl_case)
+    rng = np.random.Generator(np.random.PCG64(4242))
+    h = 0.35
+    na = int(round(n ** 3 / 64))
+    L = n * h
+    sites = rng.uniform(0.0, 1.0, (na, 3)) * L
+    spec = inputs.make_domain(n, h, no, 4, "c64", 0.02, qd, seed=4242, geo_seed=4243, wells=sites,
+                              well_depth=rng.uniform(0.5, 2.0, na), atoms=sites, n_proj=4,
+                              D=rng.uniform(-1.0, 1.0, (na, 4)), A=inputs.envelope_pulse(1000, 0.02)[:qd])
+    d = mlmd.Domain.from_spec(spec)
+    d.set_orbitals(_device_orbitals(spec.n_grid, no, spec.dV, 5, torch.complex64))
+    d.propagate(spec.A)
+    n_list = d.projector_list_length()
+    mlmd.profile_enable(d.handle, True)
+    ms, _ = _timed(lambda: d.propagate(spec.A), reps=reps)
+    out = {"case": f"{n}^3 x {no} orbitals, {na} atoms x 4 projectors", "ms_per_propagate": ms}
+    tot = 0.0
+    for k in ("stage", "scatter", "project"):
+        t, c = mlmd.profile_read(d.handle, k)
+        out[f"{k}_us_per_launch"] = 1e3 * t / max(c, 1)
+        out[f"{k}_launches"] = c
+        if k != "stage":
+            tot += t
+    # algorithmic nonlocal work: per Taylor stage one projection and one
+    # scatter of 4 real flops per (list entry, projector, orbital)
+    flops = 4 * qd * reps * 2 * n_list * 4 * 4.0 * no
+    out["list_entries_per_point"] = n_list / spec.n_grid
+    out["nonlocal_tflops_algorithmic"] = flops / (tot * 1e-3) / 1e12 if tot > 0 else None
+    print(json.dumps(out), flush=True)
     d.close()
 
 
@@ -827,6 +900,8 @@ def main():
         run_suite(args)
     elif args.stage_case:
         run_stage_case(args)
+    elif args.nl_case:
+        run_nl_case(args)
     else:
         run_ours(args)
 

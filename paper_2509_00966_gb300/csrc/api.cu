@@ -81,6 +81,37 @@ void Alloc::release_all() {
 // preceded by a projection pass over its input.
 void step_full(Domain& d, const double* Ak, double* obs_row) {
     const double dt = d.desc.dt;
+    if (d.nltc) {
+        // tensor-core nonlocal path: each stage is the local stencil kernel
+        // (out = psi + gamma h_loc w), the scatter GEMM (out += gamma v_nl w
+        // from P = <b|w>) and the projection GEMM of out for the next stage;
+        // the projections pass along Pa -> Pb -> Pa -> Pb -> Pa
+        if (!d.pa_psi) launch_nl_project_tc(d, d.psi, d.Pa);
+        const void* in = d.psi;
+        void* outs[4] = {d.wa, d.wb, d.wa, d.psi};
+        void* Pin[4] = {d.Pa, d.Pb, d.Pa, d.Pb};
+        void* Pout[4] = {d.Pb, d.Pa, d.Pb, d.Pa};
+        for (int s = 0; s < 4; ++s) {
+            StageArgs a;
+            a.w = in;
+            a.psi = d.psi;
+            a.out = outs[s];
+            a.A = Ak;
+            a.gamma_re = 0.0;
+            a.gamma_im = -dt / (double)(4 - s);
+            a.obs = (s == 0 && obs_row) ? d.obs_part : nullptr;
+            const int nblk = launch_stage(d, a);
+            if (s == 0 && obs_row) {
+                launch_obs_finish(d, d.obs_part, nblk, Ak, obs_row);
+                launch_nl_energy(d, d.Pa, obs_row);      // <psi|v_nl|psi> from P = <b|psi>
+            }
+            launch_nl_scatter_tc(d, Pin[s], outs[s], a.gamma_re, a.gamma_im);
+            launch_nl_project_tc(d, outs[s], Pout[s]);
+            in = outs[s];
+        }
+        d.pa_psi = true;
+        return;
+    }
     const bool nl = d.has_nl();
     const bool fused = nl && tma_fused_nl(d);
     if (fused && !d.pa_psi) launch_project(d, d.psi, d.Pa);
@@ -417,6 +448,7 @@ mlmd_status mlmd_domain_destroy(mlmd_domain_t dom) {
     cudaError_t e = cudaStreamSynchronize(dom->stream);
     dom->prof.destroy();
     tma_release(*dom);
+    nl_tc_release(*dom);
     delete dom;
     return e == cudaSuccess ? MLMD_OK : MLMD_ERR_CUDA;
 }

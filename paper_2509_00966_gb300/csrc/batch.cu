@@ -101,8 +101,9 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         // graph, so that the captured step is the steady-state one
         for (auto* d : b->doms) tma_autotune(*d, A_all);
         for (auto* d : b->doms)
-            if (d->has_nl() && tma_fused_nl(*d) && !d->pa_psi) {
-                launch_project(*d, d->psi, d->Pa);
+            if (d->has_nl() && !d->pa_psi && (d->nltc || tma_fused_nl(*d))) {
+                if (d->nltc) launch_nl_project_tc(*d, d->psi, d->Pa);
+                else launch_project(*d, d->psi, d->Pa);
                 d->pa_psi = true;
             }
         MLMD_CUDA(cudaStreamSynchronize(st));

@@ -307,6 +307,7 @@ void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj
     nl = Nonlocal{};
     d.Pa = d.Pb = d.Pseg = nullptr;
     d.pa_psi = false;
+    nl_tc_release(d);
     if (n_atoms == 0) {
         tma_build_nl(d, nullptr);
         return;
@@ -398,6 +399,7 @@ void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj
     d.mem.put(cursor);
     d.mem.put(ent_q);
     tma_build_nl(d, D_host);
+    nl_tc_build(d, pos_host, r_c, D_host);
 }
 
 void launch_project(Domain& d, const void* w, void* P) {

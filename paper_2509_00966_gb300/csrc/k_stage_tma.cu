@@ -156,10 +156,14 @@ template <int VP> struct Slot {
     static constexpr int YP = YM + 2 * TX * VP;
     static constexpr int N = YP + 2 * TX * VP;    // vectors per slot
     static constexpr uint32_t BYTES = N * 16;
+    static constexpr int PN = TY * TX * VP;       // vectors of a psi tile
+    static constexpr uint32_t PSI_BYTES = PN * 16;
 };
 // Scatter entry blocks have a ring of their own: the block of computed plane
 // j is brought two planes ahead of its use into slot j % ESL.
 constexpr int ESL = 3;
+// psi's centre tiles (when they come by TMA) have a ring of PSL slots.
+constexpr int PSL = 3;
 
 // Vector (x+dx, y+dy) of the plane in slot s, one of dx, dy zero, |d| <= 2.
 template <int VP>
@@ -255,7 +259,7 @@ __device__ __forceinline__ float2 swp(float2 v) { return make_float2(v.y, v.x); 
 template <typename R, int ORDER, int VP, int NP, int NSLOT, int TPP, bool OBS>
 __global__ void __launch_bounds__(64 * TPP, 2)
     k_stage_tma(const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_x,
-                const __grid_constant__ CUtensorMap tm_y, const R* __restrict__ psi_g, int psi_mode,
+                const __grid_constant__ CUtensorMap tm_y, const __grid_constant__ CUtensorMap tm_p, int psi_mode,
                 TGeo<R> G, R* out,
                 const R* __restrict__ V, const R* __restrict__ f, const double* __restrict__ Ak, TNl<R> N,
                 R gre, R gim, double* __restrict__ obs, int* err) {
@@ -269,10 +273,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     // TMA destinations on a 1024-byte boundary (the launch adds 1024 bytes of
     // slack): the swizzle pattern is a function of the address bits
     float4* ring = reinterpret_cast<float4*>(smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u));
-    float4* sP = ring + NSLOT * Slot<VP>::N;        // [maxs][NP][VP] staged <b|w>
+    float4* sPsi = ring + NSLOT * Slot<VP>::N;      // [PSL][TY][TX][VP] psi tiles
+    float4* sP = sPsi + PSL * Slot<VP>::PN;         // [maxs][NP][VP] staged <b|w>
     unsigned char* sE = reinterpret_cast<unsigned char*>(sP + N.maxs * NPV * VP);   // [ESL][scap] entry blocks
     __shared__ __align__(8) uint64_t bars[NSLOT];
     __shared__ __align__(8) uint64_t ebars[ESL];
+    __shared__ __align__(8) uint64_t pbars[PSL];
     __shared__ int64_t soff[17];                    // entry-block offsets of the column's planes (zc <= 16)
     __shared__ R sA[4];
     __shared__ int abort_sh;
@@ -290,8 +296,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     const int nplanes = nzc + 4;                    // planes z0-2 .. z0+nzc+1
     const int c0 = chunk * OCR;                     // first real of the chunk within a row
     // psi_mode 0: out = gamma h w; 1: psi is w itself (its centre tile is in
-    // the ring already); 2: each thread reads its own vectors of psi from
-    // global memory, one plane ahead (no shared-memory round trip)
+    // the ring already); 2: psi's centre tile comes by TMA with each plane
     const bool has_psi = psi_mode != 0;
     // complex64 launches take the packed path: h w as sum_n c_n w_n with the
     // complex coefficient c_n = k_n - i a_n of each stencil neighbour (k from
@@ -304,6 +309,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
         for (int s = 0; s < ESL; ++s) mbar_init(&ebars[s], 1);
+        for (int s = 0; s < PSL; ++s) mbar_init(&pbars[s], 1);
         abort_sh = 0;
         fence_proxy_async();
     }
@@ -346,6 +352,15 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         bulk_g2s(sE + (size_t)(j % ESL) * N.scap, N.sblk + eo, eb, b);
         issued_e = j + 1;
     };
+    // psi tile of computed plane j (z = z0 + j) into psi slot j % PSL
+    int issued_p = 0, waited_p = 0;                 // meaningful in thread 0
+    auto issue_psi = [&](int j) {
+        if (psi_mode != 2 || j >= nzc) return;
+        uint64_t* b = &pbars[j % PSL];
+        mbar_expect_tx(b, Slot<VP>::PSI_BYTES);
+        tma_load_4d(sPsi + (j % PSL) * Slot<VP>::PN, &tm_p, c0, x0, y0, z0 + j, b);
+        issued_p = j + 1;
+    };
 
     // shared-memory offsets (16-byte vectors) of this thread's first vector and
     // of its x-y neighbours within a slot; vector k adds 4 k
@@ -355,6 +370,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     static_assert(NVT == 1 || NVT == 2, "one or two vectors per thread");
     const int vb = jv * NVT;
     const int offC = swz<VP>(Slot<VP>::C + (ly * TX + lx) * VP, vb);
+    const int offPs = swz<VP>(pt * VP, vb);        // within a psi tile
     int offN[8];
     {
         const int dx[8] = {1, -1, 0, 0, 2, -2, 0, 0}, dy[8] = {0, 0, 1, -1, 0, 0, 2, -2};
@@ -367,6 +383,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         for (int p = 0; p < NSLOT && p < nplanes; ++p) issue(p);
         issued = min(NSLOT, nplanes);
         for (int j = 0; j < ESL - 1; ++j) issue_e(j);
+        for (int j = 0; j < PSL - 1; ++j) issue_psi(j);
     }
     // register window of the thread's vectors: q[k][0..4] = planes z-2 .. z+2
     float4 q[NVT][5];
@@ -406,20 +423,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     int64_t g = (x0 + lx) + (int64_t)G.nx * (y0 + ly) + plane_stride * z0;
     const int64_t row = 2 * (int64_t)G.ld;
     R vnext = nzc > 0 ? V[g] : (R)0;       // V one plane ahead
-    // this thread's vectors of psi (psi_mode 2) come straight from global
-    // memory: issued at the top of the plane, used after the stencil and the
-    // scatter, whose shared-memory work covers the load latency
-    const int64_t row_v = row * (int64_t)sizeof(R) / 16;      // 16-byte vectors per row
-    const float4* psi_v = psi_mode == 2 ? reinterpret_cast<const float4*>(psi_g + c0) + vb : nullptr;
     for (int i = 0; i < nzc && !aborted0; ++i, g += plane_stride) {
         // per-point global loads first, so that they overlap the plane wait
         // and the shared-memory stencil
         const R vv = vnext;
         if (i + 1 < nzc) vnext = V[g + plane_stride];
         float4 ps_cur[NVT];
-#pragma unroll
-        for (int k = 0; k < NVT; ++k)
-            ps_cur[k] = psi_mode == 2 ? __ldg(psi_v + g * row_v + k) : make_float4(0.f, 0.f, 0.f, 0.f);
         // plane z+2 (p = i+4) must have landed
         ok = wait_plane(i + 4);
         if (!ok) abort_sh = 1;
@@ -433,6 +442,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 ++issued;
             }
             issue_e(i + ESL - 1);           // into the entry slot of plane z-1
+            issue_psi(i + PSL - 1);         // into the psi slot of plane z-1
         }
         const float4* sc = ring + ((i + 2) % NSLOT) * Slot<VP>::N;    // plane z
         const float4* s4 = ring + ((i + 4) % NSLOT) * Slot<VP>::N;    // plane z+2
@@ -596,6 +606,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 }
             }
         }
+        if (psi_mode == 2) {                // psi tile of this plane (issued two planes ago)
+            if (!mbar_wait_bounded(&pbars[i % PSL], (uint32_t)((i / PSL) & 1))) abort_sh = 1;
+            if (tid == 0) waited_p = i + 1;
+#pragma unroll
+            for (int k = 0; k < NVT; ++k) ps_cur[k] = sPsi[(i % PSL) * Slot<VP>::PN + (offPs ^ k)];
+        }
 #pragma unroll
         for (int k = 0; k < NVT; ++k) {
             if constexpr (FAST) {
@@ -667,6 +683,8 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             for (int p = waited; p < issued; ++p) (void)wait_plane(p);
             for (int j = waited_e; j < issued_e; ++j)
                 (void)mbar_wait_bounded(&ebars[j % ESL], (uint32_t)((j / ESL) & 1));
+            for (int j = waited_p; j < issued_p; ++j)
+                (void)mbar_wait_bounded(&pbars[j % PSL], (uint32_t)((j / PSL) & 1));
         }
     }
     if constexpr (OBS) {
@@ -816,7 +834,7 @@ constexpr size_t kTwoCtaSmem = 113 * 1024;
 template <typename R, int VP, int NP>
 size_t smem_bytes(int maxs, int nslot, int scap) {
     const int npv = NP > 0 ? NP : 1;
-    size_t b = (size_t)nslot * Slot<VP>::N * 16;
+    size_t b = (size_t)nslot * Slot<VP>::N * 16 + (size_t)PSL * Slot<VP>::PSI_BYTES;
     if (NP > 0) b += (size_t)maxs * npv * VP * 16 + (size_t)ESL * scap;
     return b + 1024;
 }
@@ -869,7 +887,8 @@ void tma_launch(Domain& d, const StageArgs& a, const TmaMaps& m, dim3 grid, bool
     {
         ProfScope ps(d.prof, MLMD_KERNEL_STAGE, d.stream);
         const int psi_mode = a.psi == nullptr ? 0 : (a.psi == a.w ? 1 : 2);
-        kern<<<grid, 64 * tpp, smem, d.stream>>>(m.centre, m.xslab, m.yslab, static_cast<const R*>(a.psi), psi_mode, G,
+        const CUtensorMap tm_p = psi_mode == 2 ? maps_for(d, a.psi).centre : m.centre;
+        kern<<<grid, 64 * tpp, smem, d.stream>>>(m.centre, m.xslab, m.yslab, tm_p, psi_mode, G,
                                            static_cast<R*>(a.out), static_cast<const R*>(d.V),
                                            static_cast<const R*>(d.fR), a.A, N, (R)a.gamma_re, (R)a.gamma_im, a.obs,
                                            d.err_flag);
@@ -1206,14 +1225,16 @@ bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done) {
 
 // Pick the tile shape of the TMA stage kernel -- orbital-chunk width (128- or
 // 64-byte rows per CTA) and threads per grid point (4, or 8 with 128-byte
-// chunks) -- by timing a few launches of each on the domain's own data.
-// The timed launches read psi and write only the work buffer wb and the
-// projection buffer Pb, which every step overwrites before reading.
+// chunks) -- by timing a few launches of each on the domain's own buffers.
+// The timed launches read psi and the work buffer wa (as the later stages of
+// a step do) and write only the work buffer wb and the projection buffer Pb,
+// which every step overwrites before reading.
 void tma_autotune(Domain& d, const double* Ak) {
     if (!d.tma || !d.tma->ok || d.tma->tuned) return;
     TmaState& t = *d.tma;
     t.tuned = true;
-    const bool nl = d.has_nl();
+    // tensor-core nonlocal domains run the stage kernel for the local part only
+    const bool nl = d.has_nl() && !d.nltc;
     if (nl && !t.nl_ok) return;
     // MLMD_STAGE_TILE="vp,tpp" (e.g. "8,4") fixes the shape instead, for
     // reproducible profiles; ignored unless it names a valid shape here
@@ -1235,7 +1256,7 @@ void tma_autotune(Domain& d, const double* Ak) {
     if (d.c64() && (t.vp == 4 || t.vp8_ok)) cand.push_back({4, 4});
     if (cand.size() < 2) return;
     StageArgs a;
-    a.w = d.psi;
+    a.w = d.wa;
     a.psi = d.psi;
     a.out = d.wb;
     a.P = nl ? d.Pa : nullptr;

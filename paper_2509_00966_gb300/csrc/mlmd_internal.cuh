@@ -66,6 +66,7 @@ struct Geo {
 };
 
 struct TmaState;   // TMA stage-kernel state (tensor maps, tiling), k_stage_tma.cu
+struct NlTc;       // brick tables of the tensor-core nonlocal path, k_nl_tc.cu
 
 // Projector tables built on the device by set_projectors.
 struct Nonlocal {
@@ -92,8 +93,8 @@ struct Profiler {
     struct Rec { int kind; cudaEvent_t a, b; };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
-    double total_ms[MLMD_KERNEL_KINDS] = {0.0, 0.0};
-    uint64_t count[MLMD_KERNEL_KINDS] = {0, 0};
+    double total_ms[MLMD_KERNEL_KINDS] = {};
+    uint64_t count[MLMD_KERNEL_KINDS] = {};
     cudaEvent_t take();
     void begin(int kind, cudaStream_t s, Rec& r);
     void end(Rec& r, cudaStream_t s);
@@ -149,6 +150,8 @@ struct Domain {
     uint64_t launches = 0;
     Profiler prof;
     TmaState* tma = nullptr;
+    NlTc* nltc = nullptr;          // tensor-core nonlocal tables (dense-projector domains), or null
+    double nl_rc = 0.0;            // projector width r_c of the current projectors
     int* err_flag = nullptr;       // device word raised by a kernel whose bounded wait expired
     mlmd_status latched = MLMD_OK;
     std::string err;
@@ -205,6 +208,19 @@ int tma_chunk_bytes(const Domain& d);
 
 // P[a][i][o] = dV sum_q beta[q][i] w[idx[q]][o]
 void launch_project(Domain& d, const void* w, void* P);
+
+// Tensor-core nonlocal path (k_nl_tc.cu) for complex64 domains whose
+// projector spheres cover each grid point many times: brick tables built
+// from the exact lists at set_projectors; the scatter adds gamma v_nl w (from
+// P = <b|w>) to a stage output that holds the local part; the projection
+// writes P = <b|w> (zeroing P first); the energy adds <psi|v_nl|psi> from
+// P = <b|psi> to an observable row.
+bool nl_tc_wanted(const Domain& d);
+void nl_tc_build(Domain& d, const double* pos_host, double r_c, const double* D_host);
+void nl_tc_release(Domain& d);
+void launch_nl_scatter_tc(Domain& d, const void* P, void* out, double gre, double gim);
+void launch_nl_project_tc(Domain& d, const void* w, void* P);
+void launch_nl_energy(Domain& d, const void* P, double* row);
 
 // obs_dev[row][0..4] = final observables from the per-block partials
 void launch_obs_finish(Domain& d, const double* partials, int nblocks, const double* A, double* row);

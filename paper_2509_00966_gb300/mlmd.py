@@ -192,6 +192,13 @@ def set_projectors(h, pos, n_proj, r_c, r_cut, D):
                                      ctypes.c_void_p(D.ctypes.data)), h)
 
 
+def projector_list_length(h, n_atoms):
+    """Total number of (atom, grid point) list entries (reads only the offsets)."""
+    off = np.zeros(n_atoms + 1, np.int64)
+    _check(lib().mlmd_get_projector_lists(h, ctypes.c_void_p(off.ctypes.data), None, 0, None), h)
+    return int(off[-1])
+
+
 def get_projector_lists(h, n_atoms, n_proj):
     off = np.zeros(n_atoms + 1, np.int64)
     _check(lib().mlmd_get_projector_lists(h, ctypes.c_void_p(off.ctypes.data), None, 0, None), h)
@@ -341,7 +348,7 @@ def overlap_noalloc(X, Y, scale, S, stream=None):
     return S
 
 
-KERNEL = {"stage": 0, "project": 1}
+KERNEL = {"stage": 0, "project": 1, "scatter": 2}
 
 
 def profile_enable(h, enable=True):
@@ -433,6 +440,9 @@ class Domain:
 
     def projector_lists(self):
         return get_projector_lists(self.handle, self.n_atoms, self.n_proj)
+
+    def projector_list_length(self):
+        return projector_list_length(self.handle, self.n_atoms) if self.n_atoms else 0
 
     def propagate(self, A, obs=True):
         return propagate(self.handle, A, obs)
