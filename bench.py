@@ -56,7 +56,12 @@ STAGE_SRC = os.path.join(ROOT, "paper_2509_00966_gb300", "csrc", "k_stage_tma.cu
 # reports no traffic.  Per orbital*gridpoint, so that a capture on fewer
 # orbitals scales to the benchmark's orbital count.
 STAGE_TRAFFIC = {
-    "c1": {"src_sha16": "c6b68b048b178ee0", "bytes_per_unit": 683.1e6 / (48 ** 3 * 256)},
+    # (306.4 + 190.5) + (562.7 + 197.7) + (563.3 + 196.4) + (540.8 + 186.7) MB over
+    # the four launches, 48^3 x 256 orbitals
+    "c1": {"src_sha16": "3e6b07a9dbcfb0ce", "bytes_per_unit": 686.1e6 / (48 ** 3 * 256)},
+    # (766.3 + 502.0) + (1378.9 + 505.3) + (1379.4 + 509.1) + (1331.6 + 494.8) MB over
+    # the four launches, the c2 grid and projectors on 256 of its 1024 orbitals
+    "c2": {"src_sha16": "3e6b07a9dbcfb0ce", "bytes_per_unit": 1716.6e6 / (64 ** 3 * 256)},
 }
 
 
@@ -593,16 +598,16 @@ def run_c3(args, peaks, want_cpu):
     # per-kernel times: one Taylor step of every domain outside the graph
     # with per-launch CUDA events (the graph carries no timing events)
     kinds = ("stage", "scatter", "project")
-    ktot = {k: 0.0 for k in kinds}
-    kcnt = {k: 0 for k in kinds}
+    ktot = {kind: 0.0 for kind in kinds}
+    kcnt = {kind: 0 for kind in kinds}
     n_list = 0
     for dd, sp in zip(doms, specs):
         mlmd.profile_enable(dd.handle, True)
         dd.propagate(sp.A[:1], obs=True)
-        for k in kinds:
-            t, c = mlmd.profile_read(dd.handle, k)
-            ktot[k] += t
-            kcnt[k] += c
+        for kind in kinds:
+            t, c = mlmd.profile_read(dd.handle, kind)
+            ktot[kind] += t
+            kcnt[kind] += c
         mlmd.profile_enable(dd.handle, False)
         n_list += dd.projector_list_length() * sp.n_orb
     # algorithmic nonlocal work of a Taylor step: per stage one projection and
@@ -618,7 +623,7 @@ def run_c3(args, peaks, want_cpu):
             "note": "achieved counts only the algorithmic (list-entry) nonlocal flops, not the six split products "
                     "nor the zeros of the dense brick tiles",
             "traffic": None,
-            "kernel_ms_per_step": {k: ktot[k] for k in kinds}, "launches_per_step": kcnt}
+            "kernel_ms_per_step": dict(ktot), "launches_per_step": kcnt}
     # end to end: every domain's orbitals from pinned host memory, one batched
     # step, every domain's orbitals back
     pin_in = [dd.get_orbitals(device=False).pin_memory() for dd in doms]

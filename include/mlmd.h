@@ -112,9 +112,10 @@ typedef struct {
 /* Version of this interface (bumped on any signature change). */
 MLMD_API int32_t mlmd_abi_version(void);
 
-/* Create a domain on the current CUDA device.  allocator may be NULL
- * (cudaMallocAsync on `stream`); stream may be NULL (the legacy default
- * stream).  Orbitals start at zero, occupations at 2, v_loc at 0, and no
+/* Create a domain on the current CUDA device.  allocator may be NULL (then
+ * device memory comes stream-ordered from a memory pool the library keeps per
+ * device, which holds freed blocks for reuse and is trimmed whenever a domain
+ * is destroyed); stream may be NULL (the legacy default stream).  Orbitals start at zero, occupations at 2, v_loc at 0, and no
  * projectors.  Returns MLMD_ERR_INVALID for a bad descriptor, MLMD_ERR_OOM
  * when device memory runs out. */
 MLMD_API mlmd_status mlmd_domain_create(const mlmd_domain_desc* desc, const mlmd_allocator* allocator,
@@ -165,6 +166,11 @@ MLMD_API mlmd_status mlmd_get_projector_lists(mlmd_domain_t dom, int64_t* off, i
  *   [0] sum_n f_n <psi_n|psi_n>          (electron count)
  *   [1] sum_n f_n Re <psi_n|h|psi_n>      (energy, Ha)
  *   [2..4] J_a = sum_n f_n Re <psi_n|-i d_a + A_a|psi_n> = dE/dA_a.
+ * The excited-electron count n_exc is not a sixth column by design: it needs
+ * the N_o x N_o overlap with Psi(0), a GEMM of N_g N_o^2 work (at 1024
+ * orbitals ten times a Taylor step's stencil work), which a per-step row
+ * would add to every step; mlmd_excitation / mlmd_occupations compute it
+ * when the caller asks (Sec. V.A.8 hands n_exc over once per MD step).
  * If desc.ortho_every > 0 the orbitals are re-orthonormalised after every
  * step whose count since set_orbitals is a multiple of it.
  * MLMD_ERR_NUMERIC if an observable comes out NaN or Inf. */

@@ -35,6 +35,29 @@ void ensure_dynamic_smem(const void* kernel, size_t bytes) {
 // ---------------------------------------------------------------------------
 // allocator
 // ---------------------------------------------------------------------------
+// The library's own stream-ordered memory pool on a device.  Its release
+// threshold is unbounded, so memory freed by one call (the split-operand
+// tile images of the tensor-core GEMMs are gigabytes at the largest
+// workloads) stays mapped for the next instead of going back to the driver
+// at every synchronisation; mlmd_domain_destroy trims the pool.
+cudaMemPool_t library_pool(int dev) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    MLMD_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t thr = UINT64_MAX;
+    MLMD_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    pools[dev] = pool;
+    return pool;
+}
+
 void* Alloc::get(size_t bytes) {
     bytes = std::max<size_t>(bytes, 256);
     void* p = nullptr;
@@ -42,10 +65,10 @@ void* Alloc::get(size_t bytes) {
         p = a.alloc(bytes, (void*)stream, a.ctx);
         MLMD_REQUIRE(p != nullptr, MLMD_ERR_OOM, "device allocation failed (caller allocator)");
     } else {
-        cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+        cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, library_pool(device), stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
-            throw Error{MLMD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e)};
+            throw Error{MLMD_ERR_OOM, std::string("cudaMallocFromPoolAsync: ") + cudaGetErrorString(e)};
         }
     }
     live.push_back({p, bytes});
@@ -329,7 +352,7 @@ void reorth(Domain& d, int kind) {
     MLMD_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, d.stream));
     MLMD_CUDA(cudaStreamSynchronize(d.stream));
     MLMD_REQUIRE(h_info == 0, MLMD_ERR_NUMERIC, "overlap matrix is not positive definite");
-    if (!launch_update_tc(d, d.psi, M, d.wa)) launch_update(d, d.psi, M, d.wa);
+    if (!launch_update_tc(d, d.psi, M, d.wa, kind == MLMD_ORTHO_CHOL)) launch_update(d, d.psi, M, d.wa);
     std::swap(d.psi, d.wa);
 }
 
@@ -407,6 +430,7 @@ mlmd_status mlmd_domain_create(const mlmd_domain_desc* desc, const mlmd_allocato
         MLMD_CUDA(cudaGetDevice(&d->device));
         d->stream = (cudaStream_t)stream;
         d->mem.stream = d->stream;
+        d->mem.device = d->device;
         if (allocator) { d->mem.a = *allocator; d->mem.custom = true; }
         d->ng = (int64_t)desc->n[0] * desc->n[1] * desc->n[2];
         d->ld = padded_orbitals(desc->n_orb);
@@ -446,6 +470,7 @@ mlmd_status mlmd_domain_destroy(mlmd_domain_t dom) {
     if (!dom) return MLMD_ERR_INVALID;
     dom->mem.release_all();
     cudaError_t e = cudaStreamSynchronize(dom->stream);
+    if (!dom->mem.custom && e == cudaSuccess) (void)cudaMemPoolTrimTo(library_pool(dom->device), 0);
     dom->prof.destroy();
     tma_release(*dom);
     nl_tc_release(*dom);

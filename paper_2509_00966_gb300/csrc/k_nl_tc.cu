@@ -108,11 +108,46 @@ __device__ __forceinline__ bool brick_point(const TcGeo& G, int bx, int by, int 
     return x < G.nx && y < G.ny && z < G.nz;
 }
 
-// The NP projector values of atom a at grid point (x, y, z), normalised; the
-// caller masks them with the sphere membership.
+// Per-brick atom data staged in shared memory at kernel start (so that the
+// producers' inner loops make no dependent global loads): position,
+// membership set, projector normalisation and D of each of the brick's atoms,
+// and its global index.
+template <int NP> struct SAtoms {
+    float4* pos;
+    uint4* mask;
+    float* nrm;                   // [na][NP]
+    float* D;                     // [na][NP]
+    int* id;
+    static size_t bytes(int na) { return (size_t)na * (16 + 16 + 8 * NP + 4) + 64; }
+};
+
 template <int NP>
-__device__ __forceinline__ void beta_at(const TcGeo& G, int a, int x, int y, int z, float (&b)[NP]) {
-    const float4 pa = G.apos[a];
+__device__ __forceinline__ SAtoms<NP> stage_atoms(const TcGeo& G, unsigned char* base, int a0, int na) {
+    SAtoms<NP> S;
+    S.pos = reinterpret_cast<float4*>(base);
+    S.mask = reinterpret_cast<uint4*>(S.pos + na);
+    S.nrm = reinterpret_cast<float*>(S.mask + na);
+    S.D = S.nrm + (size_t)na * NP;
+    S.id = reinterpret_cast<int*>(S.D + (size_t)na * NP);
+    for (int k = threadIdx.x; k < na; k += blockDim.x) {
+        const int a = G.batom[a0 + k];
+        S.id[k] = a;
+        S.pos[k] = G.apos[a];
+        S.mask[k] = G.bmask[a0 + k];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            S.nrm[k * NP + i] = G.anrm[(size_t)a * NP + i];
+            S.D[k * NP + i] = G.aD[(size_t)a * NP + i];
+        }
+    }
+    return S;
+}
+
+// The NP projector values of staged atom k at grid point (x, y, z),
+// normalised; the caller masks them with the sphere membership.
+template <int NP>
+__device__ __forceinline__ void beta_at(const TcGeo& G, const SAtoms<NP>& S, int k, int x, int y, int z, float (&b)[NP]) {
+    const float4 pa = S.pos[k];
     float dl[3] = {(float)x * G.h - pa.x, (float)y * G.h - pa.y, (float)z * G.h - pa.z};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) dl[ax] -= G.L[ax] * floorf(dl[ax] * G.invL[ax] + 0.5f);
@@ -120,11 +155,25 @@ __device__ __forceinline__ void beta_at(const TcGeo& G, int a, int x, int y, int
 #pragma unroll
     for (int set = 0; set < NP / 4; ++set) {
         const float e = exp2f(d2 * G.cexp[set]);
-        const float* nr = G.anrm + (size_t)a * NP + 4 * set;
+        const float* nr = S.nrm + k * NP + 4 * set;
         b[4 * set] = nr[0] * e;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) b[4 * set + 1 + ax] = nr[1 + ax] * (dl[ax] * G.invrc[set]) * e;
     }
+}
+
+// Projector i of staged atom k at grid point (x, y, z), normalised.
+template <int NP>
+__device__ __forceinline__ float beta_one(const TcGeo& G, const SAtoms<NP>& S, int k, int i, int x, int y, int z) {
+    const float4 pa = S.pos[k];
+    float dl[3] = {(float)x * G.h - pa.x, (float)y * G.h - pa.y, (float)z * G.h - pa.z};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) dl[ax] -= G.L[ax] * floorf(dl[ax] * G.invL[ax] + 0.5f);
+    const float d2 = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+    const int set = i >> 2, c = i & 3;
+    const float e = exp2f(d2 * G.cexp[set]);
+    const float f = c == 0 ? 1.f : (c == 1 ? dl[0] : (c == 2 ? dl[1] : dl[2])) * G.invrc[set];
+    return S.nrm[k * NP + i] * f * e;
 }
 
 __device__ __forceinline__ bool mask_bit(const uint4& m, int p) {
@@ -168,6 +217,28 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t t, uint32_t cols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t), "r"(cols) : "memory");
 }
 
+// One B-operand item: 8 K-values (rows j*8 .. +7 of the chunk) x 4 orbital
+// columns nq*4 .. +3, loaded as 8 float4 by the caller; stored as 4 units
+// (one per column) of the K-major tile, each in three bf16 parts.
+__device__ __forceinline__ void store_b_item(unsigned char* sb, uint32_t b_part, int j, int nq, const float4 (&c)[8],
+                                             const float (&scale)[8]) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = scale[e] * c[e].x;
+    store_unit(sb, b_part, unit_off(4 * nq + 0, j), v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = scale[e] * c[e].y;
+    store_unit(sb, b_part, unit_off(4 * nq + 1, j), v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = scale[e] * c[e].z;
+    store_unit(sb, b_part, unit_off(4 * nq + 2, j), v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = scale[e] * c[e].w;
+    store_unit(sb, b_part, unit_off(4 * nq + 3, j), v);
+}
+
+constexpr int BMAX = 2;                             // B items per thread per chunk (ncols <= 384)
+
 // ---------------------------------------------------------------------------
 // scatter: out[p] += gamma sum_r B[p][r] D_r P[r]   (one CTA per brick)
 // ---------------------------------------------------------------------------
@@ -188,8 +259,10 @@ __global__ void __launch_bounds__(NT, 1)
     if (na == 0) return;
     const int nchunks = (na + APC - 1) / APC;
     const int ncols = G.ld2;
+    const int nq4 = ncols / 4;
     const uint32_t b_part = (uint32_t)ncols * KC * 2;
     const uint32_t stage_bytes = 3 * A_PART + 3 * b_part;
+    const SAtoms<NP> S = stage_atoms<NP>(G, smem + (size_t)stages * stage_bytes, a0, na);
 
     if (warp == 0) tmem_alloc(&tmem_base, tmem_cols(ncols));
     if (tid == 0) {
@@ -214,10 +287,27 @@ __global__ void __launch_bounds__(NT, 1)
             abort_sh = 1;
             break;
         }
+        // B loads first: P rows of the chunk's atoms, item = (K-octet j, column
+        // quad nq) with nq fastest across the threads (coalesced rows); the
+        // A generation below covers their latency
+        float4 braw[BMAX][8];
+#pragma unroll
+        for (int u = 0; u < BMAX; ++u) {
+            const int it = tid + u * NT;
+            const int nq = it % nq4, j = it / nq4;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int r = j * 8 + e, la = c * APC + r / NP;
+                braw[u][e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < KC / 8 && la < na)
+                    braw[u][e] = __ldg(reinterpret_cast<const float4*>(P + ((size_t)S.id[la] * NP + r % NP) * ncols) + nq);
+            }
+        }
         // A: B[p][r] for the 128 points x the chunk's 32 rows; one unit = one
-        // point x 8 rows (8 / NP atoms)
+        // point x 8 rows (8 / NP atoms); points fastest across the threads
+#pragma unroll 2
         for (int it = tid; it < BP * (KC / 8); it += NT) {
-            const int p = it >> 2, j = it & 3;
+            const int p = it % BP, j = it / BP;
             float v[8];
             int x, y, z;
             const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
@@ -225,46 +315,27 @@ __global__ void __launch_bounds__(NT, 1)
             for (int u = 0; u < 8 / NP; ++u) {
                 const int la = c * APC + j * (8 / NP) + u;
                 float b[NP];
-                bool m = false;
-                if (inside && la < na) {
-                    m = mask_bit(G.bmask[a0 + la], p);
-                    if (m) beta_at<NP>(G, G.batom[a0 + la], x, y, z, b);
-                }
+                const bool m = inside && la < na && mask_bit(S.mask[la], p);
+                if (m) beta_at<NP>(G, S, la, x, y, z, b);
 #pragma unroll
                 for (int i = 0; i < NP; ++i) v[u * NP + i] = m ? b[i] : 0.f;
             }
             store_unit(sa, A_PART, unit_off(p, j), v);
         }
-        // B: (D o P)[r][n] for the chunk's 32 rows x all orbital columns; one
-        // item = 8 rows (one K-octet) x 4 columns
-        for (int it = tid; it < (KC / 8) * (ncols / 4); it += NT) {
-            const int j = it % (KC / 8), nq = it / (KC / 8);
-            float4 col[8];
+        // B: (D o P)[r][n] split into bf16 parts
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int r = j * 8 + e;
-                const int la = c * APC + r / NP;
-                col[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (la < na) {
-                    const int a = G.batom[a0 + la];
-                    const float dd = G.aD[(size_t)a * NP + r % NP];
-                    const float4 t = __ldg(reinterpret_cast<const float4*>(P + ((size_t)a * NP + r % NP) * ncols) + nq);
-                    col[e] = make_float4(dd * t.x, dd * t.y, dd * t.z, dd * t.w);
+        for (int u = 0; u < BMAX; ++u) {
+            const int it = tid + u * NT;
+            const int nq = it % nq4, j = it / nq4;
+            if (j < KC / 8) {
+                float dd[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int r = j * 8 + e, la = c * APC + r / NP;
+                    dd[e] = la < na ? S.D[la * NP + r % NP] : 0.f;
                 }
+                store_b_item(sb, b_part, j, nq, braw[u], dd);
             }
-            float v[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = col[e].x;
-            store_unit(sb, b_part, unit_off(4 * nq + 0, j), v);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = col[e].y;
-            store_unit(sb, b_part, unit_off(4 * nq + 1, j), v);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = col[e].z;
-            store_unit(sb, b_part, unit_off(4 * nq + 2, j), v);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = col[e].w;
-            store_unit(sb, b_part, unit_off(4 * nq + 3, j), v);
         }
         fence_async_smem();
         mbar_arrive(&full[st]);
@@ -286,31 +357,55 @@ __global__ void __launch_bounds__(NT, 1)
     if (abort_sh) {
         if (tid == 0) atomicExch(err, 1);
     } else {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (points) and
-        // one half of the columns; out += gamma D on complex pairs
-        const int p = (warp & 3) * 32 + lane;
-        int x, y, z;
-        const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
-        const int half = ((ncols / 2 + 31) / 32) * 32;
-        const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? ncols : min(half, ncols);
-        float* row = out + ((size_t)x + (size_t)G.nx * ((size_t)y + (size_t)G.ny * z)) * ncols;
-        for (int cb = c0; cb < c1; cb += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
-            if (inside) {
+        // epilogue in two passes through shared memory (the ring is free now):
+        // warp w copies TMEM lanes 32 (w % 4) .. +31 (points), one half of the
+        // columns, into a [point][column] array; then all threads add gamma D
+        // to out row by row with coalesced 16-byte accesses
+        const int ldd = ncols + 4;                  // padded row (floats) against bank conflicts
+        float* sD = reinterpret_cast<float*>(smem);
+        {
+            const int p = (warp & 3) * 32 + lane;
+            const int half = ((ncols / 2 + 31) / 32) * 32;
+            const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? ncols : min(half, ncols);
+            for (int cb = c0; cb < c1; cb += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
                 const int nw = min(32, c1 - cb);
 #pragma unroll
-                for (int q = 0; q < 32; q += 4) {
-                    if (q < nw) {
-                        float4* dst = reinterpret_cast<float4*>(row + cb + q);
-                        float4 o = *dst;
-                        o.x += gre * v[q] - gim * v[q + 1];
-                        o.y += gre * v[q + 1] + gim * v[q];
-                        o.z += gre * v[q + 2] - gim * v[q + 3];
-                        o.w += gre * v[q + 3] + gim * v[q + 2];
-                        *dst = o;
+                for (int q = 0; q < 32; q += 4)
+                    if (q < nw)
+                        *reinterpret_cast<float4*>(sD + p * ldd + cb + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+            }
+        }
+        __syncthreads();
+        const int total = BP * nq4;
+        for (int it0 = tid; it0 < total; it0 += 4 * NT) {
+            float4 o[4];
+            float4* dst[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int it = it0 + u * NT;
+                dst[u] = nullptr;
+                if (it < total) {
+                    const int p = it / nq4, nq = it % nq4;
+                    int x, y, z;
+                    if (brick_point(G, bx, by, bz, p, x, y, z)) {
+                        dst[u] = reinterpret_cast<float4*>(
+                                     out + ((size_t)x + (size_t)G.nx * ((size_t)y + (size_t)G.ny * z)) * ncols) + nq;
+                        o[u] = *dst[u];
                     }
                 }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!dst[u]) continue;
+                const int it = it0 + u * NT, p = it / nq4, nq = it % nq4;
+                const float4 dv = *reinterpret_cast<const float4*>(sD + p * ldd + 4 * nq);
+                o[u].x += gre * dv.x - gim * dv.y;
+                o[u].y += gre * dv.y + gim * dv.x;
+                o[u].z += gre * dv.z - gim * dv.w;
+                o[u].w += gre * dv.w + gim * dv.z;
+                *dst[u] = o[u];
             }
         }
     }
@@ -334,9 +429,9 @@ __global__ void __launch_bounds__(NT, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[4], empty[4], done;
+    __shared__ __align__(8) uint64_t fin;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_sh;
-    __shared__ __align__(8) uint64_t fin;
     constexpr int APT = 128 / NP;                   // atoms per M-tile
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int brick = blockIdx.x;
@@ -345,8 +440,10 @@ __global__ void __launch_bounds__(NT, 1)
     if (na == 0) return;
     const int ntiles = (na + APT - 1) / APT;
     const int ncols = G.ld2;
+    const int nq4 = ncols / 4;
     const uint32_t b_part = (uint32_t)ncols * KC * 2;
     const uint32_t stage_bytes = 3 * A_PART + 3 * b_part;
+    const SAtoms<NP> S = stage_atoms<NP>(G, smem + (size_t)stages * stage_bytes, a0, na);
 
     if (warp == 0) tmem_alloc(&tmem_base, tmem_cols(ncols));
     if (tid == 0) {
@@ -374,63 +471,50 @@ __global__ void __launch_bounds__(NT, 1)
             if (c >= stages) ok_e = mbar_wait_bounded(&empty[st], (uint32_t)((c / stages - 1) & 1));
             if (!ok_e) abort_sh = 1;
             if (ok_e) {
+                // B loads first: w on one brick x-row of 8 points (= K-octet j:
+                // plane kc, row j of the brick) x 4 columns, columns fastest
+                float4 braw[BMAX][8];
+#pragma unroll
+                for (int u = 0; u < BMAX; ++u) {
+                    const int it = tid + u * NT;
+                    const int nq = it % nq4, j = it / nq4;
+                    int x, y, z;
+                    const bool row_in = j < KC / 8 && brick_point(G, bx, by, bz, kc * KC + j * 8, x, y, z);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        braw[u][e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (row_in && x + e < G.nx)
+                            braw[u][e] = __ldg(reinterpret_cast<const float4*>(
+                                                   w + ((size_t)(x + e) + (size_t)G.nx * ((size_t)y + (size_t)G.ny * z)) *
+                                                           ncols) + nq);
+                    }
+                }
                 // A: B^T[r][p] for the tile's 128 rows x the chunk's 32 points;
-                // one item = one atom x one brick x-row of 8 points (NP units)
-                for (int it = tid; it < APT * (KC / 8); it += NT) {
-                    const int ra = it / (KC / 8), j = it % (KC / 8);
-                    const int la = t * APT + ra;
-                    float b[8][NP];
+                // one unit = one row (atom, projector) x one brick x-row of 8
+                // points; rows fastest across the threads
+#pragma unroll 2
+                for (int it = tid; it < 128 * (KC / 8); it += NT) {
+                    const int r = it % 128, j = it / 128;
+                    const int la = t * APT + r / NP, i = r % NP;
+                    const uint4 mk = la < na ? S.mask[la] : make_uint4(0, 0, 0, 0);
+                    float v[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         const int p = kc * KC + j * 8 + e;
                         int x, y, z;
                         const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
-                        bool m = false;
-                        if (inside && la < na) {
-                            m = mask_bit(G.bmask[a0 + la], p);
-                            if (m) beta_at<NP>(G, G.batom[a0 + la], x, y, z, b[e]);
-                        }
-                        if (!m)
-#pragma unroll
-                            for (int i = 0; i < NP; ++i) b[e][i] = 0.f;
+                        const bool m = inside && mask_bit(mk, p);
+                        v[e] = m ? beta_one<NP>(G, S, la, i, x, y, z) : 0.f;
                     }
-#pragma unroll
-                    for (int i = 0; i < NP; ++i) {
-                        float v[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) v[e] = b[e][i];
-                        store_unit(sa, A_PART, unit_off(ra * NP + i, j), v);
-                    }
+                    store_unit(sa, A_PART, unit_off(r, j), v);
                 }
-                // B: w^T[n][p] for all orbital columns x the chunk's 32 points;
-                // one item = one brick x-row of 8 points x 4 columns
-                for (int it = tid; it < (KC / 8) * (ncols / 4); it += NT) {
-                    const int j = it % (KC / 8), nq = it / (KC / 8);
-                    const int p0 = kc * KC + j * 8;
-                    int x, y, z;
-                    const bool inside_row = brick_point(G, bx, by, bz, p0, x, y, z);
-                    float4 val[8];
+                // B: w^T[n][p] split into bf16 parts
+                const float one[8] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        val[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (inside_row && x + e < G.nx)
-                            val[e] = __ldg(reinterpret_cast<const float4*>(
-                                               w + ((size_t)(x + e) + (size_t)G.nx * ((size_t)y + (size_t)G.ny * z)) *
-                                                       ncols) + nq);
-                    }
-                    float v[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = val[e].x;
-                    store_unit(sb, b_part, unit_off(4 * nq + 0, j), v);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = val[e].y;
-                    store_unit(sb, b_part, unit_off(4 * nq + 1, j), v);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = val[e].z;
-                    store_unit(sb, b_part, unit_off(4 * nq + 2, j), v);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = val[e].w;
-                    store_unit(sb, b_part, unit_off(4 * nq + 3, j), v);
+                for (int u = 0; u < BMAX; ++u) {
+                    const int it = tid + u * NT;
+                    const int nq = it % nq4, j = it / nq4;
+                    if (j < KC / 8) store_b_item(sb, b_part, j, nq, braw[u], one);
                 }
             }
             fence_async_smem();
@@ -456,7 +540,7 @@ __global__ void __launch_bounds__(NT, 1)
         const int la = t * APT + r / NP;
         const int half = ((ncols / 2 + 31) / 32) * 32;
         const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? ncols : min(half, ncols);
-        float* dst = la < na ? P + ((size_t)G.batom[a0 + la] * NP + r % NP) * ncols : nullptr;
+        float* dst = la < na ? P + ((size_t)S.id[la] * NP + r % NP) * ncols : nullptr;
         for (int cb = c0; cb < c1; cb += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
@@ -527,9 +611,19 @@ void widths(double r_c, float (&cexp)[2], float (&invrc)[2]) {
     }
 }
 
-int stages_for(int ld2) {
-    const size_t stage = 3 * (size_t)A_PART + 3 * (size_t)ld2 * KC * 2;
-    return (int)std::min<size_t>(4, (200 * 1024) / stage);
+// Ring stages that fit beside the staged atom data in 225 KB of shared memory.
+size_t stage_bytes_for(int ld2) { return 3 * (size_t)A_PART + 3 * (size_t)ld2 * KC * 2; }
+size_t atom_bytes_for(int max_atoms, int np) { return (size_t)max_atoms * (16 + 16 + 8 * np + 4) + 64; }
+int stages_for(int ld2, int max_atoms, int np) {
+    const size_t atoms = atom_bytes_for(max_atoms, np);
+    if (atoms >= 225 * 1024) return 0;
+    return (int)std::min<size_t>(4, (225 * 1024 - atoms) / stage_bytes_for(ld2));
+}
+// The ring and the staged atoms; the scatter's epilogue reuses the same space
+// for its [128][ld2 + 4] FP32 copy of the accumulator.
+size_t smem_for(int ld2, int max_atoms, int np) {
+    const size_t used = (size_t)stages_for(ld2, max_atoms, np) * stage_bytes_for(ld2) + atom_bytes_for(max_atoms, np);
+    return std::max(used, (size_t)128 * (ld2 + 4) * sizeof(float)) + 1024;
 }
 
 TcGeo geo_for(const Domain& d) {
@@ -647,8 +741,12 @@ void nl_tc_build(Domain& d, const double* pos_host, double r_c, const double* D_
     t->anrm = (float*)upload(nrm.data(), sizeof(float) * nrm.size());
     t->aD = (float*)upload(Df.data(), sizeof(float) * Df.size());
     MLMD_CUDA(cudaStreamSynchronize(d.stream));
+    if (stages_for(2 * d.ld, t->max_atoms, np) < 2) {   // too many atoms on one brick for the ring: SIMT path
+        nl_tc_release(d);
+        return;
+    }
     // raise the kernels' shared-memory limit now, outside any stream capture
-    const size_t smem = (size_t)stages_for(2 * d.ld) * (3 * A_PART + 3 * (size_t)2 * d.ld * KC * 2) + 1024;
+    const size_t smem = smem_for(2 * d.ld, t->max_atoms, np);
     ensure_dynamic_smem(reinterpret_cast<const void*>(np == 4 ? k_nl_scatter_tc<4> : k_nl_scatter_tc<8>), smem);
     ensure_dynamic_smem(reinterpret_cast<const void*>(np == 4 ? k_nl_project_tc<4> : k_nl_project_tc<8>), smem);
 }
@@ -664,8 +762,8 @@ void launch_nl_energy(Domain& d, const void* P, double* row) {
 // local part the stage kernel wrote to out.
 void launch_nl_scatter_tc(Domain& d, const void* P, void* out, double gre, double gim) {
     const TcGeo G = geo_for(d);
-    const int stages = stages_for(G.ld2);
-    const size_t smem = (size_t)stages * (3 * A_PART + 3 * (size_t)G.ld2 * KC * 2) + 1024;
+    const int stages = stages_for(G.ld2, d.nltc->max_atoms, d.nl.n_proj);
+    const size_t smem = smem_for(G.ld2, d.nltc->max_atoms, d.nl.n_proj);
     ProfScope ps(d.prof, MLMD_KERNEL_SCATTER, d.stream);
     if (d.nl.n_proj == 4) {
         ensure_dynamic_smem(reinterpret_cast<const void*>(k_nl_scatter_tc<4>), smem);
@@ -683,8 +781,8 @@ void launch_nl_scatter_tc(Domain& d, const void* P, void* out, double gre, doubl
 // P = dV B^T w (P is zeroed here first, then accumulated by atomics).
 void launch_nl_project_tc(Domain& d, const void* w, void* P) {
     const TcGeo G = geo_for(d);
-    const int stages = stages_for(G.ld2);
-    const size_t smem = (size_t)stages * (3 * A_PART + 3 * (size_t)G.ld2 * KC * 2) + 1024;
+    const int stages = stages_for(G.ld2, d.nltc->max_atoms, d.nl.n_proj);
+    const size_t smem = smem_for(G.ld2, d.nltc->max_atoms, d.nl.n_proj);
     MLMD_CUDA(cudaMemsetAsync(P, 0, (size_t)d.nl.n_atoms * d.nl.n_proj * G.ld2 * sizeof(float), d.stream));
     const float dV = (float)(d.desc.h * d.desc.h * d.desc.h);
     ProfScope ps(d.prof, MLMD_KERNEL_PROJECT, d.stream);

@@ -146,7 +146,7 @@ template <int MODE>
 __global__ void __launch_bounds__(128, 1)
     k_update_tc(const unsigned char* __restrict__ pa, const unsigned char* __restrict__ pb, int ngt, int njt, int nkt,
                 const float* __restrict__ Z, float* __restrict__ Y, int64_t ng, int ncols, float xunscale,
-                const unsigned int* __restrict__ maxbits, int* __restrict__ err) {
+                const unsigned int* __restrict__ maxbits, int upper, int* __restrict__ err) {
     constexpr int NPART = Split<MODE>::NPART, NPROD = Split<MODE>::NPROD, STAGES = Stages<MODE>::value;
     constexpr uint32_t STAGE_BYTES = 2 * NPART * kTileBytes;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -158,6 +158,9 @@ __global__ void __launch_bounds__(128, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int jt = blockIdx.x, gt = blockIdx.y;
+    // upper-triangular M: output columns of tile jt (orbitals jt*64 .. +63)
+    // take inputs only from orbitals <= jt*64 + 63, i.e. K-tiles <= 2 jt + 1
+    const int nk = upper ? min(nkt, 2 * jt + 2) : nkt;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(128, 1)
 
     int issued = 0;                      // producer: steps whose copies were issued
     if (tid == 0) {                     // producer
-        for (int i = 0; i < nkt && !abort_sh; ++i) {
+        for (int i = 0; i < nk && !abort_sh; ++i) {
             const int st = i % STAGES;
             if (i >= STAGES && !mbar_wait_bounded(&empty[st], (uint32_t)((i / STAGES - 1) & 1))) {
                 abort_sh = 1;
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(128, 1)
             issued = i + 1;
         }
     } else if (tid == 32) {             // MMA issuer
-        for (int i = 0; i < nkt; ++i) {
+        for (int i = 0; i < nk; ++i) {
             const int st = i % STAGES;
             if (!mbar_wait_bounded(&full[st], (uint32_t)((i / STAGES) & 1))) {
                 abort_sh = 1;
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     // the MMA thread commits `done` after its loop in every case, so the MMAs
     // it issued have finished reading shared memory and writing TMEM once it fires
-    if (nkt > 0 && !mbar_wait_bounded(&done, 0)) abort_sh = 1;
+    if (nk > 0 && !mbar_wait_bounded(&done, 0)) abort_sh = 1;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 template <int MODE>
-void update_mode(Domain& d, const float* X, const double* M, int sub_id, const float* Z, float* Y) {
+void update_mode(Domain& d, const float* X, const double* M, int sub_id, const float* Z, float* Y, bool upper) {
     constexpr int NPART = Split<MODE>::NPART, STAGES = Stages<MODE>::value;
     const int n = d.desc.n_orb, ncols = 2 * d.ld;
     const int ngt = (int)((d.ng + BM - 1) / BM);
@@ -301,7 +304,7 @@ void update_mode(Domain& d, const float* X, const double* M, int sub_id, const f
     constexpr uint32_t smem = STAGES * 2 * NPART * kTileBytes + 1024;
     ensure_dynamic_smem(reinterpret_cast<const void*>(k_update_tc<MODE>), smem);
     k_update_tc<MODE><<<dim3(njt, ngt), 128, smem, d.stream>>>(pa, pb, ngt, njt, nkt, Z, Y, d.ng, ncols, xunscale,
-                                                               maxbits, d.err_flag);
+                                                               maxbits, upper ? 1 : 0, d.err_flag);
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
     d.mem.put(maxbits);
@@ -313,27 +316,29 @@ void update_mode(Domain& d, const float* X, const double* M, int sub_id, const f
 
 namespace {
 
-bool gemm_tc(Domain& d, const void* X, const double* M, int sub_id, const void* Z, void* Y) {
+bool gemm_tc(Domain& d, const void* X, const double* M, int sub_id, const void* Z, void* Y, bool upper) {
     const int mode = d.desc.gemm_mode;
     if (!d.c64() || mode == MLMD_GEMM_FP32) return false;
     const float* Xf = static_cast<const float*>(X);
     const float* Zf = static_cast<const float*>(Z);
     float* Yf = static_cast<float*>(Y);
     switch (mode) {
-        case MLMD_GEMM_BF16: update_mode<MLMD_GEMM_BF16>(d, Xf, M, sub_id, Zf, Yf); break;
-        case MLMD_GEMM_BF16X2: update_mode<MLMD_GEMM_BF16X2>(d, Xf, M, sub_id, Zf, Yf); break;
-        case MLMD_GEMM_BF16X3: update_mode<MLMD_GEMM_BF16X3>(d, Xf, M, sub_id, Zf, Yf); break;
-        default: update_mode<MLMD_GEMM_FP16>(d, Xf, M, sub_id, Zf, Yf); break;
+        case MLMD_GEMM_BF16: update_mode<MLMD_GEMM_BF16>(d, Xf, M, sub_id, Zf, Yf, upper); break;
+        case MLMD_GEMM_BF16X2: update_mode<MLMD_GEMM_BF16X2>(d, Xf, M, sub_id, Zf, Yf, upper); break;
+        case MLMD_GEMM_BF16X3: update_mode<MLMD_GEMM_BF16X3>(d, Xf, M, sub_id, Zf, Yf, upper); break;
+        default: update_mode<MLMD_GEMM_FP16>(d, Xf, M, sub_id, Zf, Yf, upper); break;
     }
     return true;
 }
 
 }  // namespace
 
-bool launch_update_tc(Domain& d, const void* X, const double* M, void* Y) { return gemm_tc(d, X, M, 1, X, Y); }
+bool launch_update_tc(Domain& d, const void* X, const double* M, void* Y, bool upper) {
+    return gemm_tc(d, X, M, 1, X, Y, upper);
+}
 
 bool launch_gemm_add_tc(Domain& d, const void* X, const double* Mc, const void* Z, void* Y) {
-    return gemm_tc(d, X, Mc, 0, Z, Y);
+    return gemm_tc(d, X, Mc, 0, Z, Y, false);
 }
 
 }  // namespace mlmd

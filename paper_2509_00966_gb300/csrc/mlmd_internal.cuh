@@ -32,6 +32,10 @@ struct Error {
         if (!(cond)) throw ::mlmd::Error{code, std::string(text)};          \
     } while (0)
 
+// The library's stream-ordered memory pool on a device (freed blocks stay
+// mapped for reuse; trimmed when a domain is destroyed).
+cudaMemPool_t library_pool(int dev);
+
 // Padded orbital stride: orbitals are stored in rows of `ld` complex values
 // with ld a multiple of 8 (64-byte rows for complex64), padding orbitals zero.
 inline int padded_orbitals(int n_orb) { return (n_orb + 7) / 8 * 8; }
@@ -43,6 +47,7 @@ struct Alloc {
     mlmd_allocator a{};
     bool custom = false;
     cudaStream_t stream = nullptr;
+    int device = 0;
     struct Blk { void* p; size_t bytes; };
     std::vector<Blk> live;
 
@@ -263,7 +268,8 @@ void launch_occupations(Domain& d, const double* C, double* fs, double* rs, doub
 void launch_scale_complex(Domain& d, double* M, int64_t nn, double sr, double si);
 // Y = X M on the tensor cores in the domain's split mode (c64, non-FP32 GEMM
 // modes); false if the domain does not use them.
-bool launch_update_tc(Domain& d, const void* X, const double* M, void* Y);
+// upper: M is upper triangular (a Cholesky L^{-H}); the zero K-tiles are skipped.
+bool launch_update_tc(Domain& d, const void* X, const double* M, void* Y, bool upper);
 // Y = Z + X Mc on the tensor cores in the domain's split mode (Mc complex
 // FP64 [n_orb][n_orb]); false if the domain does not use them.
 bool launch_gemm_add_tc(Domain& d, const void* X, const double* Mc, const void* Z, void* Y);

@@ -88,14 +88,21 @@ def test_reorth_update_tensor_cores(mode, n, n_orb, kind):
     d.close()
 
 
-@pytest.mark.parametrize("mode,tol", [("bf16x3", 2e-5), ("bf16x2", 5e-5), ("fp16", 2e-3), ("bf16", 2e-2), ("fp32", 1e-5)])
-def test_precision_form_propagation(mode, tol):
-    """The precision form at reduced size: complex64 orbitals propagated 20
-    steps with projectors and the pulse, Cholesky re-orthonormalisation every
-    10 steps with the Gram and update GEMMs in the given split mode, against
-    the FP64 oracle; orbitals, the per-step observables (electron count,
-    energy, current) and the density and current fields after the run."""
-    spec = small_spec(precision="c64", n=(16, 16, 12), n_orb=40, steps=20, n_atoms=6)
+# (mode, steps, bound on max |psi - psi_ref| with <psi|psi> = 1, relative bound
+# on the electron count / energy / current, relative bound on rho and j):
+# FP32-class modes take the stated bounds of the complex64 path (1e-5 on psi
+# after 100 steps, 1e-6 on E and J, 1e-5 on rho); the plain 16-bit modes the
+# stated 1e-3 on psi and rho.
+@pytest.mark.parametrize("mode,steps,psi_tol,obs_tol,field_tol", [
+    ("bf16x3", 100, 1e-5, 1e-6, 1e-5), ("fp32", 100, 1e-5, 1e-6, 1e-5), ("bf16x2", 100, 1e-4, 1e-5, 1e-4),
+    ("fp16", 20, 1e-3, 1e-3, 1e-3), ("bf16", 20, 1e-3, 1e-3, 1e-3)])
+def test_precision_form_propagation(mode, steps, psi_tol, obs_tol, field_tol):
+    """The precision form at reduced size: complex64 orbitals propagated with
+    projectors and the pulse, Cholesky re-orthonormalisation every 10 steps
+    with the Gram and update GEMMs in the given split mode, against the FP64
+    oracle; orbitals, the per-step observables (electron count, energy,
+    current) and the density and current fields after the run."""
+    spec = small_spec(precision="c64", n=(16, 16, 12), n_orb=40, steps=steps, n_atoms=6)
     d, V = gpu_domain(spec, gemm_mode=mode, ortho_every=10)
     od = oracle_domain(spec, V)
     psi = orbitals(spec)
@@ -104,15 +111,20 @@ def test_precision_form_propagation(mode, tol):
     out = to_numpy(d.get_orbitals())
     f = np.full(spec.n_orb, 2.0)
     ref, robs = oracle.propagate(od, psi, spec.A, spec.dt, f, ortho_every=10)
-    assert np.max(np.abs(out - ref)) <= tol * np.abs(ref).max() * 10, (mode, np.max(np.abs(out - ref)))
-    np.testing.assert_allclose(obs[:, 0], robs[:, 0], rtol=tol)
-    np.testing.assert_allclose(obs[:, 1], robs[:, 1], rtol=tol, atol=tol * np.abs(robs[:, 0]).max())
-    scale = max(np.abs(robs[:, 2:]).max(), np.abs(robs[:, 0]).max())
-    assert np.max(np.abs(obs[:, 2:] - robs[:, 2:])) <= tol * scale
     rho, j, J = d.density_current(spec.A[-1], device=False)
     rr, jr, Jr = od.density_current(ref, spec.A[-1], f)
-    assert np.max(np.abs(np.asarray(rho) - rr)) <= tol * np.abs(rr).max() * 10
-    assert np.max(np.abs(np.asarray(j) - jr)) <= tol * max(np.abs(jr).max(), np.abs(rr).max()) * 10
+    e_psi = np.max(np.abs(out - ref))
+    e_n = np.max(np.abs(obs[:, 0] - robs[:, 0]) / np.abs(robs[:, 0]))
+    e_E = np.max(np.abs(obs[:, 1] - robs[:, 1])) / np.abs(robs[:, 1]).max()
+    scale = max(np.abs(robs[:, 2:]).max(), np.abs(robs[:, 0]).max())
+    e_J = np.max(np.abs(obs[:, 2:] - robs[:, 2:])) / scale
+    e_rho = np.max(np.abs(np.asarray(rho) - rr)) / np.abs(rr).max()
+    e_j = np.max(np.abs(np.asarray(j) - jr)) / max(np.abs(jr).max(), np.abs(rr).max())
+    print(f"\n[errors] precision form {mode}, {steps} steps: psi={e_psi:.3e} norm={e_n:.3e} energy={e_E:.3e} "
+          f"current={e_J:.3e} rho={e_rho:.3e} j={e_j:.3e}", flush=True)
+    assert e_psi <= psi_tol
+    assert e_n <= obs_tol and e_E <= obs_tol and e_J <= obs_tol
+    assert e_rho <= field_tol and e_j <= field_tol
     d.close()
 
 
