@@ -109,7 +109,7 @@ void step_full(Domain& d, const double* Ak, double* obs_row) {
         // (out = psi + gamma h_loc w), the scatter GEMM (out += gamma v_nl w
         // from P = <b|w>) and the projection GEMM of out for the next stage;
         // the projections pass along Pa -> Pb -> Pa -> Pb -> Pa
-        if (!d.pa_psi) launch_nl_project_tc(d, d.psi, d.Pa);
+        if (!d.pa_psi) launch_nl_project_tc(d, d.psi, d.Pa, false);
         const void* in = d.psi;
         void* outs[4] = {d.wa, d.wb, d.wa, d.psi};
         void* Pin[4] = {d.Pa, d.Pb, d.Pa, d.Pb};
@@ -129,7 +129,7 @@ void step_full(Domain& d, const double* Ak, double* obs_row) {
                 launch_nl_energy(d, d.Pa, obs_row);      // <psi|v_nl|psi> from P = <b|psi>
             }
             launch_nl_scatter_tc(d, Pin[s], outs[s], a.gamma_re, a.gamma_im);
-            launch_nl_project_tc(d, outs[s], Pout[s]);
+            launch_nl_project_tc(d, outs[s], Pout[s], true);   // the scatter left the split output
             in = outs[s];
         }
         d.pa_psi = true;

@@ -102,7 +102,7 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         for (auto* d : b->doms) tma_autotune(*d, A_all);
         for (auto* d : b->doms)
             if (d->has_nl() && !d->pa_psi && (d->nltc || tma_fused_nl(*d))) {
-                if (d->nltc) launch_nl_project_tc(*d, d->psi, d->Pa);
+                if (d->nltc) launch_nl_project_tc(*d, d->psi, d->Pa, false);
                 else launch_project(*d, d->psi, d->Pa);
                 d->pa_psi = true;
             }

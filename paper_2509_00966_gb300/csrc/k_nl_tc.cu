@@ -3,30 +3,40 @@
 // and scatter-back as GEMMs; Sec. V.B.7: BF16 split products).
 //
 // The grid is cut into bricks of 8 x 4 x 4 = 128 points.  For one brick the
-// atoms whose spheres touch it give R = NP x (atoms) projector rows, and the
-// two halves of the nonlocal term are dense GEMMs over the brick:
+// atoms whose spheres touch it give the projector rows, and the two halves
+// of the nonlocal term are dense GEMMs over the brick:
 //
 //   scatter     out[p][n] += gamma sum_r B[p][r] (D o P)[r][n]     (M = points, K = rows,   N = orbital reals)
 //   projection  P[r][n]   += dV    sum_p B[p][r] w[p][n]           (M = rows,   K = points, N = orbital reals)
 //
 // with B[p][r] = beta_r(p) if p lies in the sphere of r's atom, else 0.
 // Complex orbitals enter as interleaved (re, im) real columns (B is real).
-// B is not stored: the producer warps evaluate the projector values of the
-// brick's atoms in FP32 (min-image displacement, Gaussian, normalisation
+// B is not stored: the producer threads evaluate the projector values of
+// the brick's atoms in FP32 (min-image displacement, Gaussian, normalisation
 // from the FP64 lists) and mask them with a per-(brick, atom) 128-bit
 // membership set taken from the exact FP64 neighbour lists, so sphere
-// membership is the lists' own.  Every FP32 operand is split into three
-// bf16 parts (x ~ x0 + x1 + x2) and the six products with i + j <= 2 are
-// accumulated in FP32 in tensor memory, smallest first.
+// membership is the lists' own.
 //
-// Pipeline of one CTA (256 threads): every thread produces its share of a
-// K-chunk (32 rows or 32 points) into a ring stage in shared memory, fences
-// the writes into the async proxy and arrives on the stage's `full`
-// barrier; thread 0 waits for `full`, issues the MMAs of the chunk and
-// commits them to the stage's `empty` barrier, which the producers wait on
-// before they refill the stage.  Every wait is bounded (~2 s); on expiry
-// the CTA raises the domain's error word, waits (bounded) for its MMAs and
-// frees its tensor memory.
+// Every FP32 operand x is split exactly into three bf16 parts by truncation
+// (x0 = the top 8 significand bits of x, x1 those of x - x0, x2 = x - x0 -
+// x1, which has at most 8 significant bits), and the six products x_i y_j
+// with i + j <= 2 are accumulated in FP32 in tensor memory, smallest first.
+// The operands that do not depend on the brick's geometry are split once per
+// stage, not once per CTA: D o P (small) by k_nl_split_P into one 16-byte
+// slab per (atom, column) -- the NP projector values, padded to 8 -- and the
+// stage output w by the scatter's epilogue (or k_nl_split_w) into one 16-byte
+// slab per (brick x-row of 8 points, column).  Both reach shared memory by
+// bulk copies in a layout whose 8 x 16-byte core matrices are 8 consecutive
+// columns of one K-octet ([K-octet][column][8 values]).
+//
+// Pipeline of one CTA (256 threads): thread 0 issues the bulk copies of a
+// K-chunk into a ring stage; every thread generates its share of the
+// projector tile into the same stage, fences the writes into the async proxy
+// and arrives on the stage's `full` barrier; thread 0 waits for `full`,
+// issues the MMAs of the chunk and commits them to the stage's `empty`
+// barrier, which guards the next refill.  Every wait is bounded (~2 s); on
+// expiry the CTA raises the domain's error word, waits (bounded) for its
+// copies and MMAs and frees its tensor memory.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -46,6 +56,9 @@ struct NlTc {
     float4* apos = nullptr;       // [n_atoms] positions (x, y, z, 0), bohr
     float* anrm = nullptr;        // [n_atoms][NP] normalisation of each projector (dV sum b^2 = 1)
     float* aD = nullptr;          // [n_atoms][NP] strengths D
+    uint16_t* P3a = nullptr;      // split D o P of the projections in Pa: [3][n_atoms][2 ld][8] bf16
+    uint16_t* P3b = nullptr;      // the same for Pb
+    uint16_t* w3 = nullptr;       // split stage output: [3][nbricks][16][2 ld][8] bf16
 };
 
 namespace {
@@ -53,7 +66,7 @@ namespace {
 using namespace tc;
 
 constexpr int BX = 8, BY = 4, BZ = 4, BP = BX * BY * BZ;   // brick of 128 points
-constexpr int KC = 32;                                      // K elements per ring stage
+constexpr int KC = 32;                                      // K elements per ring stage (4 K-octets)
 constexpr uint32_t A_PART = 128 * KC * 2;                   // one 16-bit part of a 128-row A tile
 constexpr int NT = 256;                                     // threads per CTA
 
@@ -71,10 +84,14 @@ struct TcGeo {
     const float* aD;
 };
 
-// Byte offset of the 16-byte unit (row, K-octet j) of a K-major canonical
-// tile with K = 32: core matrices of 8 rows x 16 bytes, the four K-cores of
-// a row group adjacent (LBO = 128 B), row groups 512 B apart (SBO).
+// A tiles (128 rows x K = 32): byte offset of the 16-byte unit (row, K-octet
+// j); core matrices of 8 rows x 16 bytes, the four K-cores of a row group
+// adjacent (LBO = 128 B), row groups 512 B apart (SBO).
 __device__ __forceinline__ uint32_t unit_off(int row, int j) { return (uint32_t)((row >> 3) * 512 + j * 128 + (row & 7) * 16); }
+
+// B tiles (ncols rows x K = 32) are [K-octet j][column n][16 bytes]: the core
+// matrix of columns 8g .. 8g+7 is 128 contiguous bytes (SBO = 128 B), and
+// the K-octets are ncols x 16 bytes apart (LBO).
 
 // tcgen05.mma kind::f16 instruction descriptor: FP32 accumulator, BF16 A and
 // B, K-major, M = 128, N given (a multiple of 16, at most 256).
@@ -82,22 +99,31 @@ __device__ __forceinline__ uint32_t idesc_n(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void bf16x3(float x, uint16_t (&p)[3]) { split_value<MLMD_GEMM_BF16X3>(x, 1.f, p); }
+// Exact split of two FP32 values into three bf16 parts each (truncation: the
+// top 16 bits of x, then of the remainders), packed pairwise into 32-bit
+// words (part of x0 in the low half).
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& h, uint32_t& m, uint32_t& l) {
+    const uint32_t u0 = __float_as_uint(x0), u1 = __float_as_uint(x1);
+    h = __byte_perm(u0, u1, 0x7632);
+    const float r0 = x0 - __uint_as_float(u0 & 0xffff0000u), r1 = x1 - __uint_as_float(u1 & 0xffff0000u);
+    const uint32_t v0 = __float_as_uint(r0), v1 = __float_as_uint(r1);
+    m = __byte_perm(v0, v1, 0x7632);
+    const float s0 = r0 - __uint_as_float(v0 & 0xffff0000u), s1 = r1 - __uint_as_float(v1 & 0xffff0000u);
+    l = __byte_perm(__float_as_uint(s0), __float_as_uint(s1), 0x7632);
+}
 
-// Eight FP32 values -> one 16-byte unit per bf16 part, stored at base + part * part_bytes + off.
+// Eight FP32 values -> one 16-byte unit per bf16 part.
+__device__ __forceinline__ void split8(const float (&v)[8], uint4 (&q)[3]) {
+    split2(v[0], v[1], q[0].x, q[1].x, q[2].x);
+    split2(v[2], v[3], q[0].y, q[1].y, q[2].y);
+    split2(v[4], v[5], q[0].z, q[1].z, q[2].z);
+    split2(v[6], v[7], q[0].w, q[1].w, q[2].w);
+}
 __device__ __forceinline__ void store_unit(unsigned char* base, uint32_t part_bytes, uint32_t off, const float (&v)[8]) {
-    uint16_t q[8][3];
+    uint4 q[3];
+    split8(v, q);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) bf16x3(v[e], q[e]);
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        uint4 u;
-        u.x = (uint32_t)q[0][s] | ((uint32_t)q[1][s] << 16);
-        u.y = (uint32_t)q[2][s] | ((uint32_t)q[3][s] << 16);
-        u.z = (uint32_t)q[4][s] | ((uint32_t)q[5][s] << 16);
-        u.w = (uint32_t)q[6][s] | ((uint32_t)q[7][s] << 16);
-        *reinterpret_cast<uint4*>(base + (size_t)s * part_bytes + off) = u;
-    }
+    for (int s = 0; s < 3; ++s) *reinterpret_cast<uint4*>(base + (size_t)s * part_bytes + off) = q[s];
 }
 
 // Grid coordinates of point p of brick (bx, by, bz); false outside the grid.
@@ -110,15 +136,13 @@ __device__ __forceinline__ bool brick_point(const TcGeo& G, int bx, int by, int 
 
 // Per-brick atom data staged in shared memory at kernel start (so that the
 // producers' inner loops make no dependent global loads): position,
-// membership set, projector normalisation and D of each of the brick's atoms,
+// membership set and projector normalisation of each of the brick's atoms,
 // and its global index.
 template <int NP> struct SAtoms {
     float4* pos;
     uint4* mask;
     float* nrm;                   // [na][NP]
-    float* D;                     // [na][NP]
     int* id;
-    static size_t bytes(int na) { return (size_t)na * (16 + 16 + 8 * NP + 4) + 64; }
 };
 
 template <int NP>
@@ -127,18 +151,14 @@ __device__ __forceinline__ SAtoms<NP> stage_atoms(const TcGeo& G, unsigned char*
     S.pos = reinterpret_cast<float4*>(base);
     S.mask = reinterpret_cast<uint4*>(S.pos + na);
     S.nrm = reinterpret_cast<float*>(S.mask + na);
-    S.D = S.nrm + (size_t)na * NP;
-    S.id = reinterpret_cast<int*>(S.D + (size_t)na * NP);
+    S.id = reinterpret_cast<int*>(S.nrm + (size_t)na * NP);
     for (int k = threadIdx.x; k < na; k += blockDim.x) {
         const int a = G.batom[a0 + k];
         S.id[k] = a;
         S.pos[k] = G.apos[a];
         S.mask[k] = G.bmask[a0 + k];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            S.nrm[k * NP + i] = G.anrm[(size_t)a * NP + i];
-            S.D[k * NP + i] = G.aD[(size_t)a * NP + i];
-        }
+        for (int i = 0; i < NP; ++i) S.nrm[k * NP + i] = G.anrm[(size_t)a * NP + i];
     }
     return S;
 }
@@ -162,20 +182,6 @@ __device__ __forceinline__ void beta_at(const TcGeo& G, const SAtoms<NP>& S, int
     }
 }
 
-// Projector i of staged atom k at grid point (x, y, z), normalised.
-template <int NP>
-__device__ __forceinline__ float beta_one(const TcGeo& G, const SAtoms<NP>& S, int k, int i, int x, int y, int z) {
-    const float4 pa = S.pos[k];
-    float dl[3] = {(float)x * G.h - pa.x, (float)y * G.h - pa.y, (float)z * G.h - pa.z};
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) dl[ax] -= G.L[ax] * floorf(dl[ax] * G.invL[ax] + 0.5f);
-    const float d2 = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
-    const int set = i >> 2, c = i & 3;
-    const float e = exp2f(d2 * G.cexp[set]);
-    const float f = c == 0 ? 1.f : (c == 1 ? dl[0] : (c == 2 ? dl[1] : dl[2])) * G.invrc[set];
-    return S.nrm[k * NP + i] * f * e;
-}
-
 __device__ __forceinline__ bool mask_bit(const uint4& m, int p) {
     const uint32_t w = p < 32 ? m.x : p < 64 ? m.y : p < 96 ? m.z : m.w;
     return (w >> (p & 31)) & 1u;
@@ -186,17 +192,17 @@ __device__ __forceinline__ bool mask_bit(const uint4& m, int p) {
 __device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t a_base, uint32_t b_base, uint32_t b_part, int ncols,
                                             bool first) {
     const int n0 = ncols <= 256 ? ncols : ((ncols / 2 + 15) / 16) * 16;
+    const uint32_t lbo_b = (uint32_t)ncols * 16;
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
             const uint64_t ad = smem_desc(a_base + prod_a(p, 6) * A_PART + kk * 256, 128, 512);
             const uint32_t acc = (first && kk == 0 && p == 0) ? 0u : 1u;
-            const uint32_t bp = b_base + prod_b(p, 6) * b_part + kk * 256;
-            mma_f16(tmem, ad, smem_desc(bp, 128, 512), idesc_n(n0), acc);
+            const uint32_t bp = b_base + prod_b(p, 6) * b_part + kk * 2 * lbo_b;
+            mma_f16(tmem, ad, smem_desc(bp, lbo_b, 128), idesc_n(n0), acc);
             if (ncols > n0)
-                mma_f16(tmem + (uint32_t)n0, ad, smem_desc(bp + (uint32_t)(n0 >> 3) * 512, 128, 512),
-                        idesc_n(ncols - n0), acc);
+                mma_f16(tmem + (uint32_t)n0, ad, smem_desc(bp + (uint32_t)n0 * 16, lbo_b, 128), idesc_n(ncols - n0), acc);
         }
 }
 
@@ -217,57 +223,45 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t t, uint32_t cols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t), "r"(cols) : "memory");
 }
 
-// One B-operand item: 8 K-values (rows j*8 .. +7 of the chunk) x 4 orbital
-// columns nq*4 .. +3, loaded as 8 float4 by the caller; stored as 4 units
-// (one per column) of the K-major tile, each in three bf16 parts.
-__device__ __forceinline__ void store_b_item(unsigned char* sb, uint32_t b_part, int j, int nq, const float4 (&c)[8],
-                                             const float (&scale)[8]) {
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = scale[e] * c[e].x;
-    store_unit(sb, b_part, unit_off(4 * nq + 0, j), v);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = scale[e] * c[e].y;
-    store_unit(sb, b_part, unit_off(4 * nq + 1, j), v);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = scale[e] * c[e].z;
-    store_unit(sb, b_part, unit_off(4 * nq + 2, j), v);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = scale[e] * c[e].w;
-    store_unit(sb, b_part, unit_off(4 * nq + 3, j), v);
+// Offsets (bf16 elements) of the split arrays' 16-byte slab rows.
+__device__ __forceinline__ size_t p3_off(int part, int n_atoms, int atom, int ncols) {
+    return (((size_t)part * n_atoms + atom) * ncols) * 8;
 }
-
-constexpr int BMAX = 2;                             // B items per thread per chunk (ncols <= 384)
+__device__ __forceinline__ size_t w3_off(int part, int nbricks, int brick, int xrow, int ncols) {
+    return ((((size_t)part * nbricks + brick) * 16 + xrow) * ncols) * 8;
+}
 
 // ---------------------------------------------------------------------------
 // scatter: out[p] += gamma sum_r B[p][r] D_r P[r]   (one CTA per brick)
+// K-octet j of chunk c is atom c*4 + j (its NP projectors, padded to 8).
+// The epilogue also writes the split, transposed output of the brick (the
+// projection's B operand).
 // ---------------------------------------------------------------------------
 template <int NP>
 __global__ void __launch_bounds__(NT, 1)
-    k_nl_scatter_tc(TcGeo G, const float* __restrict__ P, float* __restrict__ out, float gre, float gim, int stages,
-                    int* __restrict__ err) {
+    k_nl_scatter_tc(TcGeo G, const uint16_t* __restrict__ P3, int n_atoms, float* __restrict__ out,
+                    uint16_t* __restrict__ w3, int nbricks, float gre, float gim, int stages, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[4], empty[4], done;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_sh;
-    constexpr int APC = KC / NP;                    // atoms per K-chunk
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int brick = blockIdx.x;
     const int bx = brick % G.nbx, by = (brick / G.nbx) % G.nby, bz = brick / (G.nbx * G.nby);
     const int a0 = G.bstart[brick], na = G.bstart[brick + 1] - a0;
-    if (na == 0) return;
-    const int nchunks = (na + APC - 1) / APC;
+    if (na == 0) return;                            // nothing to add; the projection skips the brick too
     const int ncols = G.ld2;
-    const int nq4 = ncols / 4;
     const uint32_t b_part = (uint32_t)ncols * KC * 2;
     const uint32_t stage_bytes = 3 * A_PART + 3 * b_part;
+    const uint32_t slab = (uint32_t)ncols * 16;     // one K-octet of one B part
+    const int nchunks = (na + 3) / 4;
     const SAtoms<NP> S = stage_atoms<NP>(G, smem + (size_t)stages * stage_bytes, a0, na);
 
     if (warp == 0) tmem_alloc(&tmem_base, tmem_cols(ncols));
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
-            mbar_init(&full[s], NT);
+            mbar_init(&full[s], NT + 1);            // every thread, plus thread 0's expect_tx
             mbar_init(&empty[s], 1);
         }
         mbar_init(&done, 1);
@@ -278,6 +272,7 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
+    int issued = 0, consumed = 0;                   // thread 0: chunks whose copies were issued / landed
 
     for (int c = 0; c < nchunks; ++c) {
         const int st = c % stages;
@@ -287,55 +282,39 @@ __global__ void __launch_bounds__(NT, 1)
             abort_sh = 1;
             break;
         }
-        // B loads first: P rows of the chunk's atoms, item = (K-octet j, column
-        // quad nq) with nq fastest across the threads (coalesced rows); the
-        // A generation below covers their latency
-        float4 braw[BMAX][8];
+        const int nv = min(4, na - c * 4);          // atoms of this chunk
+        if (tid == 0) {                              // B: the split D o P slabs of the chunk's atoms
+            mbar_expect_tx(&full[st], (uint32_t)nv * 3 * slab);
+#pragma unroll 1
+            for (int j = 0; j < nv; ++j)
 #pragma unroll
-        for (int u = 0; u < BMAX; ++u) {
-            const int it = tid + u * NT;
-            const int nq = it % nq4, j = it / nq4;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int r = j * 8 + e, la = c * APC + r / NP;
-                braw[u][e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < KC / 8 && la < na)
-                    braw[u][e] = __ldg(reinterpret_cast<const float4*>(P + ((size_t)S.id[la] * NP + r % NP) * ncols) + nq);
-            }
+                for (int s = 0; s < 3; ++s)
+                    bulk_load(sb + (size_t)s * b_part + (size_t)j * slab, P3 + p3_off(s, n_atoms, S.id[c * 4 + j], ncols),
+                              slab, &full[st]);
+            issued = c + 1;
         }
-        // A: B[p][r] for the 128 points x the chunk's 32 rows; one unit = one
-        // point x 8 rows (8 / NP atoms); points fastest across the threads
+        // K-octets of missing atoms (last chunk) are zero in B
+        for (int e = tid; e < (4 - nv) * 3 * ncols; e += NT) {
+            const int s = e / ((4 - nv) * ncols), r = e % ((4 - nv) * ncols);
+            *reinterpret_cast<uint4*>(sb + (size_t)s * b_part + (size_t)(nv + r / ncols) * slab + (size_t)(r % ncols) * 16) =
+                make_uint4(0, 0, 0, 0);
+        }
+        // A: B[p][r] for the 128 points x the chunk's 4 atoms; one unit = one
+        // point x one atom (its NP projectors, padded to 8); points fastest
 #pragma unroll 2
-        for (int it = tid; it < BP * (KC / 8); it += NT) {
+        for (int it = tid; it < BP * 4; it += NT) {
             const int p = it % BP, j = it / BP;
-            float v[8];
+            const int la = c * 4 + j;
             int x, y, z;
             const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
-#pragma unroll
-            for (int u = 0; u < 8 / NP; ++u) {
-                const int la = c * APC + j * (8 / NP) + u;
+            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (inside && la < na && mask_bit(S.mask[la], p)) {
                 float b[NP];
-                const bool m = inside && la < na && mask_bit(S.mask[la], p);
-                if (m) beta_at<NP>(G, S, la, x, y, z, b);
+                beta_at<NP>(G, S, la, x, y, z, b);
 #pragma unroll
-                for (int i = 0; i < NP; ++i) v[u * NP + i] = m ? b[i] : 0.f;
+                for (int i = 0; i < NP; ++i) v[i] = b[i];
             }
             store_unit(sa, A_PART, unit_off(p, j), v);
-        }
-        // B: (D o P)[r][n] split into bf16 parts
-#pragma unroll
-        for (int u = 0; u < BMAX; ++u) {
-            const int it = tid + u * NT;
-            const int nq = it % nq4, j = it / nq4;
-            if (j < KC / 8) {
-                float dd[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int r = j * 8 + e, la = c * APC + r / NP;
-                    dd[e] = la < na ? S.D[la * NP + r % NP] : 0.f;
-                }
-                store_b_item(sb, b_part, j, nq, braw[u], dd);
-            }
         }
         fence_async_smem();
         mbar_arrive(&full[st]);
@@ -344,12 +323,17 @@ __global__ void __launch_bounds__(NT, 1)
                 abort_sh = 1;
                 break;
             }
+            consumed = c + 1;
             tc_fence_after();
             issue_chunk(tmem, smem_u32(sa), smem_u32(sb), b_part, ncols, c == 0);
             mma_commit(&empty[st]);
         }
     }
-    if (tid == 0) mma_commit(&done);                // fires when every MMA issued above has completed
+    if (tid == 0) {
+        mma_commit(&done);                          // fires when every MMA issued above has completed
+        for (int c = consumed; c < issued; ++c)     // after an abort: copies still in flight land first
+            (void)mbar_wait_bounded(&full[c % stages], (uint32_t)((c / stages) & 1));
+    }
     const bool ok = mbar_wait_bounded(&done, 0);
     tc_fence_after();
     if (!ok) abort_sh = 1;
@@ -357,13 +341,15 @@ __global__ void __launch_bounds__(NT, 1)
     if (abort_sh) {
         if (tid == 0) atomicExch(err, 1);
     } else {
-        // epilogue in two passes through shared memory (the ring is free now):
-        // warp w copies TMEM lanes 32 (w % 4) .. +31 (points), one half of the
-        // columns, into a [point][column] array; then all threads add gamma D
-        // to out row by row with coalesced 16-byte accesses
+        // epilogue through shared memory (the ring is free now): warp w copies
+        // TMEM lanes 32 (w % 4) .. +31 (points), one half of the columns, into
+        // a [point][column] array; all threads then add gamma D to out row by
+        // row with coalesced 16-byte accesses, keeping the new values in the
+        // array; last the array goes out transposed and split into bf16 parts,
+        // one 16-byte slab per (brick x-row, column), for the projection
         const int ldd = ncols + 4;                  // padded row (floats) against bank conflicts
         float* sD = reinterpret_cast<float*>(smem);
-        {
+        if (nchunks > 0) {
             const int p = (warp & 3) * 32 + lane;
             const int half = ((ncols / 2 + 31) / 32) * 32;
             const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? ncols : min(half, ncols);
@@ -378,7 +364,7 @@ __global__ void __launch_bounds__(NT, 1)
             }
         }
         __syncthreads();
-        const int total = BP * nq4;
+        const int nq4 = ncols / 4, total = BP * nq4;
         for (int it0 = tid; it0 < total; it0 += 4 * NT) {
             float4 o[4];
             float4* dst[4];
@@ -386,6 +372,7 @@ __global__ void __launch_bounds__(NT, 1)
             for (int u = 0; u < 4; ++u) {
                 const int it = it0 + u * NT;
                 dst[u] = nullptr;
+                o[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (it < total) {
                     const int p = it / nq4, nq = it % nq4;
                     int x, y, z;
@@ -398,15 +385,33 @@ __global__ void __launch_bounds__(NT, 1)
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (!dst[u]) continue;
-                const int it = it0 + u * NT, p = it / nq4, nq = it % nq4;
-                const float4 dv = *reinterpret_cast<const float4*>(sD + p * ldd + 4 * nq);
-                o[u].x += gre * dv.x - gim * dv.y;
-                o[u].y += gre * dv.y + gim * dv.x;
-                o[u].z += gre * dv.z - gim * dv.w;
-                o[u].w += gre * dv.w + gim * dv.z;
-                *dst[u] = o[u];
+                const int it = it0 + u * NT;
+                if (it >= total) continue;
+                const int p = it / nq4, nq = it % nq4;
+                float4* sp = reinterpret_cast<float4*>(sD + p * ldd + 4 * nq);
+                if (dst[u] && nchunks > 0) {
+                    const float4 dv = *sp;
+                    o[u].x += gre * dv.x - gim * dv.y;
+                    o[u].y += gre * dv.y + gim * dv.x;
+                    o[u].z += gre * dv.z - gim * dv.w;
+                    o[u].w += gre * dv.w + gim * dv.z;
+                    *dst[u] = o[u];
+                }
+                *sp = o[u];                          // the brick's output (zero outside the grid)
             }
+        }
+        __syncthreads();
+        // split output: item = (x-row r, column n), columns fastest
+        for (int it = tid; it < 16 * ncols; it += NT) {
+            const int r = it / ncols, n = it % ncols;
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = sD[(r * 8 + e) * ldd + n];
+            uint4 q[3];
+            split8(v, q);
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+                *reinterpret_cast<uint4*>(w3 + w3_off(s, nbricks, brick, r, ncols) + (size_t)n * 8) = q[s];
         }
     }
     tc_fence_before();
@@ -420,11 +425,12 @@ __global__ void __launch_bounds__(NT, 1)
 // ---------------------------------------------------------------------------
 // projection: P[r] += dV sum_p B[p][r] w[p]   (one CTA per brick; the rows of
 // the brick's atoms in M-tiles of 128, each accumulated over the 128 points
-// in four K-chunks and drained with vector atomics)
+// in four K-chunks -- chunk kc is the brick's z-plane kc, K-octet j its
+// x-row y = j -- and drained with vector atomics)
 // ---------------------------------------------------------------------------
 template <int NP>
 __global__ void __launch_bounds__(NT, 1)
-    k_nl_project_tc(TcGeo G, const float* __restrict__ w, float* __restrict__ P, float dV, int stages,
+    k_nl_project_tc(TcGeo G, const uint16_t* __restrict__ w3, int nbricks, float* __restrict__ P, float dV, int stages,
                     int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -440,7 +446,6 @@ __global__ void __launch_bounds__(NT, 1)
     if (na == 0) return;
     const int ntiles = (na + APT - 1) / APT;
     const int ncols = G.ld2;
-    const int nq4 = ncols / 4;
     const uint32_t b_part = (uint32_t)ncols * KC * 2;
     const uint32_t stage_bytes = 3 * A_PART + 3 * b_part;
     const SAtoms<NP> S = stage_atoms<NP>(G, smem + (size_t)stages * stage_bytes, a0, na);
@@ -448,7 +453,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (warp == 0) tmem_alloc(&tmem_base, tmem_cols(ncols));
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
-            mbar_init(&full[s], NT);
+            mbar_init(&full[s], NT + 1);            // every thread, plus thread 0's expect_tx
             mbar_init(&empty[s], 1);
         }
         mbar_init(&done, 1);
@@ -460,6 +465,7 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
+    int issued = 0, consumed = 0;                   // thread 0: chunks whose copies were issued / landed
 
     for (int t = 0; t < ntiles; ++t) {
         for (int kc = 0; kc < BP / KC; ++kc) {
@@ -471,56 +477,47 @@ __global__ void __launch_bounds__(NT, 1)
             if (c >= stages) ok_e = mbar_wait_bounded(&empty[st], (uint32_t)((c / stages - 1) & 1));
             if (!ok_e) abort_sh = 1;
             if (ok_e) {
-                // B loads first: w on one brick x-row of 8 points (= K-octet j:
-                // plane kc, row j of the brick) x 4 columns, columns fastest
-                float4 braw[BMAX][8];
+                if (tid == 0) {                      // B: the split w of x-rows 4 kc .. 4 kc + 3, all columns
+                    mbar_expect_tx(&full[st], 3 * b_part);
 #pragma unroll
-                for (int u = 0; u < BMAX; ++u) {
-                    const int it = tid + u * NT;
-                    const int nq = it % nq4, j = it / nq4;
-                    int x, y, z;
-                    const bool row_in = j < KC / 8 && brick_point(G, bx, by, bz, kc * KC + j * 8, x, y, z);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        braw[u][e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (row_in && x + e < G.nx)
-                            braw[u][e] = __ldg(reinterpret_cast<const float4*>(
-                                                   w + ((size_t)(x + e) + (size_t)G.nx * ((size_t)y + (size_t)G.ny * z)) *
-                                                           ncols) + nq);
-                    }
+                    for (int s = 0; s < 3; ++s)
+                        bulk_load(sb + (size_t)s * b_part, w3 + w3_off(s, nbricks, brick, kc * 4, ncols), b_part,
+                                  &full[st]);
+                    issued = c + 1;
                 }
                 // A: B^T[r][p] for the tile's 128 rows x the chunk's 32 points;
-                // one unit = one row (atom, projector) x one brick x-row of 8
-                // points; rows fastest across the threads
-#pragma unroll 2
-                for (int it = tid; it < 128 * (KC / 8); it += NT) {
-                    const int r = it % 128, j = it / 128;
-                    const int la = t * APT + r / NP, i = r % NP;
+                // one item = one atom x one brick x-row of 8 points (NP units)
+                for (int it = tid; it < APT * 4; it += NT) {
+                    const int ra = it % APT, j = it / APT;
+                    const int la = t * APT + ra;
+                    float b[8][NP];
                     const uint4 mk = la < na ? S.mask[la] : make_uint4(0, 0, 0, 0);
-                    float v[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         const int p = kc * KC + j * 8 + e;
                         int x, y, z;
-                        const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
-                        const bool m = inside && mask_bit(mk, p);
-                        v[e] = m ? beta_one<NP>(G, S, la, i, x, y, z) : 0.f;
-                    }
-                    store_unit(sa, A_PART, unit_off(r, j), v);
-                }
-                // B: w^T[n][p] split into bf16 parts
-                const float one[8] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+                        const bool m = brick_point(G, bx, by, bz, p, x, y, z) && mask_bit(mk, p);
+                        if (m) {
+                            beta_at<NP>(G, S, la, x, y, z, b[e]);
+                        } else {
 #pragma unroll
-                for (int u = 0; u < BMAX; ++u) {
-                    const int it = tid + u * NT;
-                    const int nq = it % nq4, j = it / nq4;
-                    if (j < KC / 8) store_b_item(sb, b_part, j, nq, braw[u], one);
+                            for (int i = 0; i < NP; ++i) b[e][i] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) {
+                        float v[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[e] = b[e][i];
+                        store_unit(sa, A_PART, unit_off(ra * NP + i, j), v);
+                    }
                 }
             }
             fence_async_smem();
             mbar_arrive(&full[st]);         // always, so that the issuing thread's wait ends
             if (tid == 0) {
                 if (!abort_sh && mbar_wait_bounded(&full[st], (uint32_t)((c / stages) & 1))) {
+                    consumed = c + 1;
                     tc_fence_after();
                     issue_chunk(tmem, smem_u32(sa), smem_u32(sb), b_part, ncols, kc == 0);
                     mma_commit(&empty[st]);
@@ -557,8 +554,10 @@ __global__ void __launch_bounds__(NT, 1)
         __syncthreads();                    // TMEM read before the next tile's MMAs overwrite it
         tc_fence_after();
     }
-    // every MMA this CTA issued has completed before its tensor memory is freed
+    // every copy and MMA of this CTA has completed before its memory is freed
     if (tid == 0) {
+        for (int c = consumed; c < issued; ++c)
+            (void)mbar_wait_bounded(&full[c % stages], (uint32_t)((c / stages) & 1));
         mma_commit(&fin);
         if (!mbar_wait_bounded(&fin, 0)) abort_sh = 1;
         if (abort_sh) atomicExch(err, 1);
@@ -568,6 +567,46 @@ __global__ void __launch_bounds__(NT, 1)
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, tmem_cols(ncols));
+    }
+}
+
+// P3[s][a][n][0..7] = part s of D_ai P[a][i][n] for i < NP (zero for i >= NP)
+template <int NP>
+__global__ void __launch_bounds__(256) k_nl_split_P(const float* __restrict__ P, const float* __restrict__ D, int n_atoms,
+                                                    int ncols, uint16_t* __restrict__ P3) {
+    const int64_t total = (int64_t)n_atoms * ncols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / ncols), n = (int)(e % ncols);
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < NP; ++i) v[i] = D[(size_t)a * NP + i] * P[((size_t)a * NP + i) * ncols + n];
+        uint4 q[3];
+        split8(v, q);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) *reinterpret_cast<uint4*>(P3 + p3_off(s, n_atoms, a, ncols) + (size_t)n * 8) = q[s];
+    }
+}
+
+// w3 of a state that did not come out of the scatter kernel: one CTA per
+// brick, item = (x-row r, column n), columns fastest; zero outside the grid.
+__global__ void __launch_bounds__(256) k_nl_split_w(TcGeo G, const float* __restrict__ w, int nbricks,
+                                                    uint16_t* __restrict__ w3) {
+    const int brick = blockIdx.x, ncols = G.ld2;
+    const int bx = brick % G.nbx, by = (brick / G.nbx) % G.nby, bz = brick / (G.nbx * G.nby);
+    for (int it = threadIdx.x; it < 16 * ncols; it += blockDim.x) {
+        const int r = it / ncols, n = it % ncols;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            int x, y, z;
+            v[e] = brick_point(G, bx, by, bz, r * 8 + e, x, y, z)
+                       ? w[((size_t)x + (size_t)G.nx * ((size_t)y + (size_t)G.ny * z)) * ncols + n]
+                       : 0.f;
+        }
+        uint4 q[3];
+        split8(v, q);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) *reinterpret_cast<uint4*>(w3 + w3_off(s, nbricks, brick, r, ncols) + (size_t)n * 8) = q[s];
     }
 }
 
@@ -595,8 +634,6 @@ __global__ void __launch_bounds__(512) k_nl_energy(const float* __restrict__ P, 
     }
 }
 
-// Minimum-image displacement along one axis as the list builder computes it
-// (FP64; the host copy of the formula, for the normalisation constants).
 double host_min_image(int c, double h, double p, double L) {
     const double t = (double)c * h - p;
     return t - L * std::floor(t / L + 0.5);
@@ -613,7 +650,7 @@ void widths(double r_c, float (&cexp)[2], float (&invrc)[2]) {
 
 // Ring stages that fit beside the staged atom data in 225 KB of shared memory.
 size_t stage_bytes_for(int ld2) { return 3 * (size_t)A_PART + 3 * (size_t)ld2 * KC * 2; }
-size_t atom_bytes_for(int max_atoms, int np) { return (size_t)max_atoms * (16 + 16 + 8 * np + 4) + 64; }
+size_t atom_bytes_for(int max_atoms, int np) { return (size_t)max_atoms * (16 + 16 + 4 * np + 4) + 64; }
 int stages_for(int ld2, int max_atoms, int np) {
     const size_t atoms = atom_bytes_for(max_atoms, np);
     if (atoms >= 225 * 1024) return 0;
@@ -659,7 +696,8 @@ bool nl_tc_wanted(const Domain& d) {
 void nl_tc_release(Domain& d) {
     if (!d.nltc) return;
     NlTc& t = *d.nltc;
-    for (void* p : {(void*)t.bstart, (void*)t.batom, (void*)t.bmask, (void*)t.apos, (void*)t.anrm, (void*)t.aD})
+    for (void* p : {(void*)t.bstart, (void*)t.batom, (void*)t.bmask, (void*)t.apos, (void*)t.anrm, (void*)t.aD,
+                    (void*)t.P3a, (void*)t.P3b, (void*)t.w3})
         if (p) d.mem.put(p);
     delete d.nltc;
     d.nltc = nullptr;
@@ -740,6 +778,10 @@ void nl_tc_build(Domain& d, const double* pos_host, double r_c, const double* D_
     t->apos = (float4*)upload(pos.data(), sizeof(float4) * pos.size());
     t->anrm = (float*)upload(nrm.data(), sizeof(float) * nrm.size());
     t->aD = (float*)upload(Df.data(), sizeof(float) * Df.size());
+    const size_t p3 = (size_t)3 * na * 2 * d.ld * 8 * sizeof(uint16_t);
+    t->P3a = (uint16_t*)d.mem.get(p3);
+    t->P3b = (uint16_t*)d.mem.get(p3);
+    t->w3 = (uint16_t*)d.mem.get((size_t)3 * t->nbricks * 16 * 2 * d.ld * 8 * sizeof(uint16_t));
     MLMD_CUDA(cudaStreamSynchronize(d.stream));
     if (stages_for(2 * d.ld, t->max_atoms, np) < 2) {   // too many atoms on one brick for the ring: SIMT path
         nl_tc_release(d);
@@ -759,43 +801,48 @@ void launch_nl_energy(Domain& d, const void* P, double* row) {
 }
 
 // out += gamma sum_r B (D o P): the nonlocal half of a stage, on top of the
-// local part the stage kernel wrote to out.
+// local part the stage kernel wrote to out; P is Pa or Pb, whose split copy
+// (P3a / P3b) the projection left behind.  Also leaves the split output in
+// w3 for the projection of out.
 void launch_nl_scatter_tc(Domain& d, const void* P, void* out, double gre, double gim) {
     const TcGeo G = geo_for(d);
-    const int stages = stages_for(G.ld2, d.nltc->max_atoms, d.nl.n_proj);
-    const size_t smem = smem_for(G.ld2, d.nltc->max_atoms, d.nl.n_proj);
+    NlTc& t = *d.nltc;
+    const int np = d.nl.n_proj;
+    const int stages = stages_for(G.ld2, t.max_atoms, np);
+    const size_t smem = smem_for(G.ld2, t.max_atoms, np);
+    const uint16_t* P3 = P == d.Pa ? t.P3a : t.P3b;
     ProfScope ps(d.prof, MLMD_KERNEL_SCATTER, d.stream);
-    if (d.nl.n_proj == 4) {
-        ensure_dynamic_smem(reinterpret_cast<const void*>(k_nl_scatter_tc<4>), smem);
-        k_nl_scatter_tc<4><<<d.nltc->nbricks, NT, smem, d.stream>>>(G, (const float*)P, (float*)out, (float)gre,
-                                                                    (float)gim, stages, d.err_flag);
-    } else {
-        ensure_dynamic_smem(reinterpret_cast<const void*>(k_nl_scatter_tc<8>), smem);
-        k_nl_scatter_tc<8><<<d.nltc->nbricks, NT, smem, d.stream>>>(G, (const float*)P, (float*)out, (float)gre,
-                                                                    (float)gim, stages, d.err_flag);
-    }
+    auto kern = np == 4 ? k_nl_scatter_tc<4> : k_nl_scatter_tc<8>;
+    kern<<<t.nbricks, NT, smem, d.stream>>>(G, P3, d.nl.n_atoms, (float*)out, t.w3, t.nbricks, (float)gre, (float)gim,
+                                            stages, d.err_flag);
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
 }
 
-// P = dV B^T w (P is zeroed here first, then accumulated by atomics).
-void launch_nl_project_tc(Domain& d, const void* w, void* P) {
+// P = dV B^T w (zeroed first, accumulated by atomics), then its split copy
+// D o P for the next scatter.  w3_ready: the scatter just wrote w's split
+// copy; otherwise it is made here.
+void launch_nl_project_tc(Domain& d, const void* w, void* P, bool w3_ready) {
     const TcGeo G = geo_for(d);
-    const int stages = stages_for(G.ld2, d.nltc->max_atoms, d.nl.n_proj);
-    const size_t smem = smem_for(G.ld2, d.nltc->max_atoms, d.nl.n_proj);
-    MLMD_CUDA(cudaMemsetAsync(P, 0, (size_t)d.nl.n_atoms * d.nl.n_proj * G.ld2 * sizeof(float), d.stream));
-    const float dV = (float)(d.desc.h * d.desc.h * d.desc.h);
+    NlTc& t = *d.nltc;
+    const int np = d.nl.n_proj;
+    const int stages = stages_for(G.ld2, t.max_atoms, np);
+    const size_t smem = smem_for(G.ld2, t.max_atoms, np);
     ProfScope ps(d.prof, MLMD_KERNEL_PROJECT, d.stream);
-    if (d.nl.n_proj == 4) {
-        ensure_dynamic_smem(reinterpret_cast<const void*>(k_nl_project_tc<4>), smem);
-        k_nl_project_tc<4><<<d.nltc->nbricks, NT, smem, d.stream>>>(G, (const float*)w, (float*)P, dV, stages,
-                                                                    d.err_flag);
-    } else {
-        ensure_dynamic_smem(reinterpret_cast<const void*>(k_nl_project_tc<8>), smem);
-        k_nl_project_tc<8><<<d.nltc->nbricks, NT, smem, d.stream>>>(G, (const float*)w, (float*)P, dV, stages,
-                                                                    d.err_flag);
+    if (!w3_ready) {
+        k_nl_split_w<<<t.nbricks, 256, 0, d.stream>>>(G, (const float*)w, t.nbricks, t.w3);
+        d.launches++;
     }
-    d.launches++;
+    MLMD_CUDA(cudaMemsetAsync(P, 0, (size_t)d.nl.n_atoms * np * G.ld2 * sizeof(float), d.stream));
+    const float dV = (float)(d.desc.h * d.desc.h * d.desc.h);
+    auto kern = np == 4 ? k_nl_project_tc<4> : k_nl_project_tc<8>;
+    kern<<<t.nbricks, NT, smem, d.stream>>>(G, t.w3, t.nbricks, (float*)P, dV, stages, d.err_flag);
+    uint16_t* P3 = P == d.Pa ? t.P3a : t.P3b;
+    const int64_t items = (int64_t)d.nl.n_atoms * G.ld2;
+    const int blocks = (int)std::min<int64_t>((items + 255) / 256, 4096);
+    if (np == 4) k_nl_split_P<4><<<blocks, 256, 0, d.stream>>>((const float*)P, t.aD, d.nl.n_atoms, G.ld2, P3);
+    else k_nl_split_P<8><<<blocks, 256, 0, d.stream>>>((const float*)P, t.aD, d.nl.n_atoms, G.ld2, P3);
+    d.launches += 2;
     MLMD_CUDA(cudaGetLastError());
 }
 

@@ -217,14 +217,16 @@ void launch_project(Domain& d, const void* w, void* P);
 // Tensor-core nonlocal path (k_nl_tc.cu) for complex64 domains whose
 // projector spheres cover each grid point many times: brick tables built
 // from the exact lists at set_projectors; the scatter adds gamma v_nl w (from
-// P = <b|w>) to a stage output that holds the local part; the projection
-// writes P = <b|w> (zeroing P first); the energy adds <psi|v_nl|psi> from
-// P = <b|psi> to an observable row.
+// P = <b|w>, P being Pa or Pb) to a stage output that holds the local part
+// and leaves the output's split copy for the projection; the projection
+// writes P = <b|w> (zeroing P first; w3_ready says the scatter just made w's
+// split copy) and the split copy of D o P; the energy adds <psi|v_nl|psi>
+// from P = <b|psi> to an observable row.
 bool nl_tc_wanted(const Domain& d);
 void nl_tc_build(Domain& d, const double* pos_host, double r_c, const double* D_host);
 void nl_tc_release(Domain& d);
 void launch_nl_scatter_tc(Domain& d, const void* P, void* out, double gre, double gim);
-void launch_nl_project_tc(Domain& d, const void* w, void* P);
+void launch_nl_project_tc(Domain& d, const void* w, void* P, bool w3_ready);
 void launch_nl_energy(Domain& d, const void* P, double* row);
 
 // obs_dev[row][0..4] = final observables from the per-block partials
