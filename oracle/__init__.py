@@ -17,6 +17,11 @@ What each function follows (paper sections and equations):
 * ``Domain.project``         Sec. V.B.5 GEMM form of the nonlocal term.
 * ``Domain.observables``     energy and current through the same projections
                              (Sec. V.B.5, last paragraph).
+* ``nl_gauge=True``          velocity-gauge projectors b e^{-iA.(r-R_a)}: Eq. 3's
+                             minimal coupling carried onto v_nl, whose current
+                             gains the commutator part from the moment
+                             projections ``Domain.project_moment`` (Sec. V.B.5,
+                             last paragraph).
 * ``overlap``/``reorth``     Eq. 5's Psi^dagger Psi product; Cholesky or
                              Loewdin re-orthonormalisation.
 * ``ks_correction``          Eq. 5: Psi(t) -= delta Psi(0) Psi^dagger(0) Psi(t),
@@ -64,7 +69,8 @@ class _CDomain(ctypes.Structure):
         ("n", ctypes.c_int32 * 3), ("h", ctypes.c_double), ("n_orb", ctypes.c_int32),
         ("fd_order", ctypes.c_int32), ("V", ctypes.c_void_p), ("n_atoms", ctypes.c_int32),
         ("n_proj", ctypes.c_int32), ("off", ctypes.c_void_p), ("idx", ctypes.c_void_p),
-        ("beta", ctypes.c_void_p), ("D", ctypes.c_void_p),
+        ("beta", ctypes.c_void_p), ("D", ctypes.c_void_p), ("nl_gauge", ctypes.c_int32),
+        ("pos", ctypes.c_void_p),
     ]
 
 
@@ -80,9 +86,10 @@ def lib():
             D = ctypes.POINTER(_CDomain)
             L.orc_gradient.argtypes = [D, ctypes.c_int, P, P]
             L.orc_apply_hloc.argtypes = [D, P, P, P]
-            L.orc_project.argtypes = [D, P, P]
-            L.orc_scatter.argtypes = [D, P, P]
-            L.orc_apply_vnl.argtypes = [D, P, P, P]
+            L.orc_project.argtypes = [D, P, P, P]
+            L.orc_project_moment.argtypes = [D, P, ctypes.c_int, P, P]
+            L.orc_scatter.argtypes = [D, P, P, P]
+            L.orc_apply_vnl.argtypes = [D, P, P, P, P]
             L.orc_apply_h.argtypes = [D, P, P, P, P]
             L.orc_taylor4.argtypes = [D, P, ctypes.c_double, ctypes.c_int, P, P, P, P]
             L.orc_taylor4_adjoint.argtypes = [D, P, ctypes.c_double, P, P, P, P]
@@ -146,7 +153,8 @@ def projector_values(n, h, pos, off, idx, n_proj, r_c):
 class Domain:
     """One periodic domain: grid, local potential, projectors."""
 
-    def __init__(self, n, h, n_orb, fd_order, V, atoms=None, n_proj=0, r_c=1.2, r_cut=3.0, D=None):
+    def __init__(self, n, h, n_orb, fd_order, V, atoms=None, n_proj=0, r_c=1.2, r_cut=3.0, D=None,
+                 nl_gauge=False):
         self.n = tuple(int(v) for v in n)
         self.h = float(h)
         self.n_orb = int(n_orb)
@@ -178,16 +186,19 @@ class Domain:
         self._c.idx = _p(self.idx)
         self._c.beta = _p(np.ascontiguousarray(self.beta))
         self._c.D = _p(self.D)
+        self.nl_gauge = bool(nl_gauge)
+        self._c.nl_gauge = int(self.nl_gauge)
+        self._c.pos = _p(self.atoms) if len(self.atoms) else None
         self._beta_keep = self.beta
         self._proj = np.zeros(max(1, self._c.n_atoms * max(self.n_proj, 1) * self.n_orb), np.complex128)
 
     @classmethod
-    def from_spec(cls, spec, V=None, n_orb=None):
+    def from_spec(cls, spec, V=None, n_orb=None, nl_gauge=False):
         from paper_2509_00966_gb300.inputs import gaussian_wells
         if V is None:
             V = gaussian_wells(spec.n, spec.h, spec.wells, spec.well_depth, spec.well_width)
         return cls(spec.n, spec.h, n_orb or spec.n_orb, spec.fd_order, V, spec.atoms, spec.n_proj,
-                   spec.r_c, spec.r_cut, spec.D)
+                   spec.r_c, spec.r_cut, spec.D, nl_gauge=nl_gauge)
 
     # -- helpers ---------------------------------------------------------
     def _check(self, psi):
@@ -214,10 +225,12 @@ class Domain:
         lib().orc_apply_hloc(ctypes.byref(self._c), _p(self._A(A)), _p(psi), _p(out))
         return out
 
-    def apply_vnl(self, psi):
+    def apply_vnl(self, psi, A=None):
+        """v_nl psi; with velocity-gauge projectors at field A (None: A = 0)."""
         psi = self._check(psi)
         out = self._like(psi)
-        lib().orc_apply_vnl(ctypes.byref(self._c), _p(psi), _p(out), _p(self._proj))
+        Ac = None if A is None else self._A(A)
+        lib().orc_apply_vnl(ctypes.byref(self._c), None if Ac is None else _p(Ac), _p(psi), _p(out), _p(self._proj))
         return out
 
     def apply_h(self, psi, A):
@@ -226,12 +239,23 @@ class Domain:
         lib().orc_apply_h(ctypes.byref(self._c), _p(self._A(A)), _p(psi), _p(out), _p(self._proj))
         return out
 
-    def project(self, psi):
-        """<beta_ai|psi_o> as complex [n_atoms, n_proj, n_orb]."""
+    def project(self, psi, A=None):
+        """<beta~_ai|psi_o> as complex [n_atoms, n_proj, n_orb] (beta~ = beta,
+        or beta e^{-iA.(r-R_a)} with velocity-gauge projectors at field A)."""
         psi = self._check(psi)
         out = np.zeros((self._c.n_atoms, self.n_proj, self.n_orb), np.complex128)
         if self.n_proj:
-            lib().orc_project(ctypes.byref(self._c), _p(psi), _p(out))
+            Ac = None if A is None else self._A(A)
+            lib().orc_project(ctypes.byref(self._c), None if Ac is None else _p(Ac), _p(psi), _p(out))
+        return out
+
+    def project_moment(self, psi, A, axis):
+        """<(r - R_a)_axis beta~_ai|psi_o>, complex [n_atoms, n_proj, n_orb]."""
+        psi = self._check(psi)
+        out = np.zeros((self._c.n_atoms, self.n_proj, self.n_orb), np.complex128)
+        if self.n_proj:
+            Ac = self._A(A)
+            lib().orc_project_moment(ctypes.byref(self._c), _p(Ac), int(axis), _p(psi), _p(out))
         return out
 
     def taylor4(self, psi, A, dt, local_only=False):
@@ -387,7 +411,11 @@ def adjoint(dom: Domain, psi_init, psi_ref, A, dt, ckpt_every):
       dL/dA_{k,a} = 2 Re sum_j c_j sum_{p<j} <h^{j-1-p} lam_{k+1} | (-i G_a + A_a) h^p psi_k>
       dL/dV(r)   += 2 Re sum_j c_j sum_{p<j} sum_o conj(h^{j-1-p} lam)(r) (h^p psi_k)(r)
     with Euclidean inner products (no dV) and lam_N = dL/dpsi*(T) = -2 dV psi_ref C.
-    Returns (loss, dL_dA [n_steps, 3], dL_dV [N_g])."""
+    Returns (loss, dL_dA [n_steps, 3], dL_dV [N_g]).  Real projectors only:
+    with velocity-gauge projectors dh/dA gains the nonlocal commutator, which
+    this contraction does not carry."""
+    if dom.nl_gauge and dom.n_proj:
+        raise NotImplementedError("adjoint with velocity-gauge projectors")
     psi_init = _c128(psi_init)
     psi_ref = _c128(psi_ref)
     A = np.asarray(A, np.float64).reshape(-1, 3)

@@ -13,6 +13,16 @@
  *     h = 1/2 (-i grad + A)^2 + v_loc(r) + v_nl
  *       = -1/2 lap - i A.grad + 1/2 |A|^2 + v_loc + sum_{a,i} |b_ai> D_ai <b_ai|
  *     with <b|psi> = dV sum_r b(r) psi(r) (b real).
+ *   Velocity-gauge projectors (optional, nl_gauge = 1): for uniform A the
+ *   minimal coupling of Eq. 3 is the unitary map h(A) = e^{-iA.r} h(0) e^{iA.r}
+ *   of the kinetic term; carried onto v_nl it gives each projector the
+ *   factor e^{-i A.(r - R_a)}, referred to the atom by the minimum image:
+ *     v_nl(A) = sum_{a,i} |b~_ai> D_ai <b~_ai|,  b~_ai(r) = e^{-i A.(r - R_a)} b_ai(r),
+ *   and the current J = dE/dA then has the nonlocal commutator part
+ *     dE_nl/dA_x = sum_o f_o sum_ai D_ai 2 Re( i conj(P_aio) Q_aio^x ),
+ *     P = <b~|psi>,  Q^x = <(r - R_a)_x b~|psi>
+ *   (the nonlocal correction to energy and current of Sec. V.B.5, last
+ *   paragraph).
  *   Periodic finite differences of order p (p = 2 or 4) for lap and grad.
  *   Time step: 4th-order Taylor expansion of exp(-i dt h(t_k)), A taken at
  *   the step midpoint t_k = (k + 1/2) dt as in Eq. 2.
@@ -45,6 +55,8 @@ typedef struct {
     const int32_t* idx;      /* [off[n_atoms]] grid indices */
     const double* beta;      /* [off[n_atoms]][n_proj] projector values */
     const double* D;         /* [n_atoms][n_proj] strengths */
+    int32_t nl_gauge;        /* 1: velocity-gauge projectors b e^{-i A.(r - R_a)} */
+    const double* pos;       /* [n_atoms][3] atom positions (read when nl_gauge) */
 } orc_domain;
 
 static int64_t n_grid(const orc_domain* d) { return (int64_t)d->n[0] * d->n[1] * d->n[2]; }
@@ -132,9 +144,31 @@ void orc_apply_hloc(const orc_domain* d, const double A[3], const double* psi_in
             }
 }
 
-/* proj[a][i][o] = <b_ai|psi_o> = dV sum_r b_ai(r) psi_o(r)   (Eq. 5 form: one
- * projection GEMM per atom).  proj is complex [n_atoms][n_proj][n_orb]. */
-void orc_project(const orc_domain* d, const double* psi_in, double* proj_) {
+/* Minimum-image displacement r_g - R_a of grid point g from atom a, with
+ * the wrap of the neighbour lists. */
+static void entry_delta(const orc_domain* d, int a, int32_t g, double dl[3]) {
+    const int coord[3] = {g % d->n[0], (g / d->n[0]) % d->n[1], g / (d->n[0] * d->n[1])};
+    for (int ax = 0; ax < 3; ++ax) {
+        const double L = (double)d->n[ax] * d->h;
+        const double t = (double)coord[ax] * d->h - d->pos[3 * a + ax];
+        dl[ax] = t - L * floor(t / L + 0.5);
+    }
+}
+
+/* Gauge factor of projector a at grid point g: e^{-i A.(r_g - R_a)} in the
+ * velocity gauge, 1 for real projectors (or A == NULL). */
+static cplx gauge_factor(const orc_domain* d, const double* A, int a, int32_t g) {
+    if (!d->nl_gauge || !A) return 1.0;
+    double dl[3];
+    entry_delta(d, a, g, dl);
+    const double th = A[0] * dl[0] + A[1] * dl[1] + A[2] * dl[2];
+    return cos(th) - I * sin(th);
+}
+
+/* proj[a][i][o] = <b~_ai|w_o psi_o> = dV sum_r conj(b~_ai(r)) w(r) psi_o(r)
+ * (Eq. 5 form: one projection GEMM per atom), w = 1, or the displacement
+ * component (r - R_a)_axis when axis >= 0.  proj: complex [n_atoms][n_proj][n_orb]. */
+static void project_impl(const orc_domain* d, const double* A, int axis, const double* psi_in, double* proj_) {
     const cplx* in = (const cplx*)psi_in;
     cplx* proj = (cplx*)proj_;
     const int no = d->n_orb, np = d->n_proj;
@@ -145,10 +179,16 @@ void orc_project(const orc_domain* d, const double* psi_in, double* proj_) {
             for (int o = 0; o < no; ++o) proj[((int64_t)a * np + i) * no + o] = 0.0;
         for (int64_t q = d->off[a]; q < d->off[a + 1]; ++q) {
             const cplx* row = in + (int64_t)d->idx[q] * no;
+            cplx wq = conj(gauge_factor(d, A, a, d->idx[q]));
+            if (axis >= 0) {
+                double dl[3];
+                entry_delta(d, a, d->idx[q], dl);
+                wq *= dl[axis];
+            }
             for (int i = 0; i < np; ++i) {
                 double b = d->beta[q * np + i];
                 cplx* pr = proj + ((int64_t)a * np + i) * no;
-                for (int o = 0; o < no; ++o) pr[o] += b * row[o];
+                for (int o = 0; o < no; ++o) pr[o] += b * wq * row[o];
             }
         }
         for (int i = 0; i < np; ++i)
@@ -156,8 +196,18 @@ void orc_project(const orc_domain* d, const double* psi_in, double* proj_) {
     }
 }
 
-/* out += sum_{a,i} b_ai D_ai proj[a][i]   (scatter-back GEMM). */
-void orc_scatter(const orc_domain* d, const double* proj_, double* out_) {
+/* proj = <b~|psi> at field A (A may be NULL for real projectors). */
+void orc_project(const orc_domain* d, const double* A, const double* psi_in, double* proj_) {
+    project_impl(d, A, -1, psi_in, proj_);
+}
+
+/* proj = <(r - R_a)_axis b~|psi>: the moment projection of the nonlocal current. */
+void orc_project_moment(const orc_domain* d, const double* A, int axis, const double* psi_in, double* proj_) {
+    project_impl(d, A, axis, psi_in, proj_);
+}
+
+/* out += sum_{a,i} b~_ai D_ai proj[a][i]   (scatter-back GEMM). */
+void orc_scatter(const orc_domain* d, const double* A, const double* proj_, double* out_) {
     const cplx* proj = (const cplx*)proj_;
     cplx* out = (cplx*)out_;
     const int no = d->n_orb, np = d->n_proj;
@@ -169,24 +219,24 @@ void orc_scatter(const orc_domain* d, const double* proj_, double* out_) {
                 cplx acc = 0.0;
                 for (int i = 0; i < np; ++i)
                     acc += d->beta[q * np + i] * d->D[(int64_t)a * np + i] * proj[((int64_t)a * np + i) * no + o];
-                out[(int64_t)d->idx[q] * no + o] += acc;
+                out[(int64_t)d->idx[q] * no + o] += gauge_factor(d, A, a, d->idx[q]) * acc;
             }
 }
 
-/* out = v_nl psi */
-void orc_apply_vnl(const orc_domain* d, const double* psi_in, double* out_, double* work_proj) {
+/* out = v_nl(A) psi */
+void orc_apply_vnl(const orc_domain* d, const double* A, const double* psi_in, double* out_, double* work_proj) {
     memset(out_, 0, sizeof(cplx) * (size_t)n_grid(d) * d->n_orb);
     if (d->n_atoms == 0 || d->n_proj == 0) return;
-    orc_project(d, psi_in, work_proj);
-    orc_scatter(d, work_proj, out_);
+    orc_project(d, A, psi_in, work_proj);
+    orc_scatter(d, A, work_proj, out_);
 }
 
 /* out = h(A) psi (local + nonlocal), Eq. 3.  work_proj: [n_atoms*n_proj*n_orb] complex. */
 void orc_apply_h(const orc_domain* d, const double A[3], const double* psi_in, double* out_, double* work_proj) {
     orc_apply_hloc(d, A, psi_in, out_);
     if (d->n_atoms == 0 || d->n_proj == 0) return;
-    orc_project(d, psi_in, work_proj);
-    orc_scatter(d, work_proj, out_);
+    orc_project(d, A, psi_in, work_proj);
+    orc_scatter(d, A, work_proj, out_);
 }
 
 /* psi_out = sum_{j=0..4} (-i dt)^j / j! h^j psi_in, with u_j = h u_{j-1}
@@ -244,14 +294,14 @@ void orc_orbital_norms(const orc_domain* d, const double* psi_in, double* nrm) {
     }
 }
 
-/* N_nl psi = (1 - i dt/2 v_nl) psi, then each orbital rescaled to the norm
+/* N_nl psi = (1 - i dt/2 v_nl(A)) psi, then each orbital rescaled to the norm
  * it had before the factor (the normalising denominator of Eq. 2). */
-static void apply_nnl(const orc_domain* d, double dt, cplx* psi, cplx* tmp, double* work_proj,
+static void apply_nnl(const orc_domain* d, const double A[3], double dt, cplx* psi, cplx* tmp, double* work_proj,
                       double* nrm_before, double* nrm_after) {
     const int no = d->n_orb;
     const int64_t ng = n_grid(d);
     orc_orbital_norms(d, (const double*)psi, nrm_before);
-    orc_apply_vnl(d, (const double*)psi, (double*)tmp, work_proj);
+    orc_apply_vnl(d, A, (const double*)psi, (double*)tmp, work_proj);
     for (int64_t t = 0; t < ng * no; ++t) psi[t] += (-0.5 * I * dt) * tmp[t];
     orc_orbital_norms(d, (const double*)psi, nrm_after);
     for (int64_t g = 0; g < ng; ++g)
@@ -266,15 +316,16 @@ void orc_split_step(const orc_domain* d, const double A[3], double dt, const dou
     cplx* out = (cplx*)psi_out;
     const int has_nl = d->n_atoms > 0 && d->n_proj > 0;
     if (psi_out != psi_in) memcpy(out, psi_in, sizeof(cplx) * (size_t)N);
-    if (has_nl) apply_nnl(d, dt, out, (cplx*)work, work_proj, nrm_before, nrm_after);
+    if (has_nl) apply_nnl(d, A, dt, out, (cplx*)work, work_proj, nrm_before, nrm_after);
     orc_taylor4(d, A, dt, 1, (const double*)out, (double*)out, work, work_proj);
-    if (has_nl) apply_nnl(d, dt, out, (cplx*)work, work_proj, nrm_before, nrm_after);
+    if (has_nl) apply_nnl(d, A, dt, out, (cplx*)work, work_proj, nrm_before, nrm_after);
 }
 
 /* Observables of psi under h(A):
  *   obs[0] = sum_o f_o <psi_o|psi_o>                 (electron count)
  *   obs[1] = sum_o f_o Re <psi_o| h |psi_o>            (energy)
  *   obs[2+a] = sum_o f_o Re <psi_o| -i G_a + A_a |psi_o>  (current J = dE/dA)
+ *              + the nonlocal commutator part with velocity-gauge projectors
  * work: N_g*n_orb complex. */
 void orc_observables(const orc_domain* d, const double A[3], const double* f, const double* psi_in,
                      double* obs, double* work, double* work_proj) {
@@ -303,6 +354,24 @@ void orc_observables(const orc_domain* d, const double A[3], const double* f, co
                 s += f[o] * creal(conj(c) * (-I * gp[g * no + o] + A[ax] * c));
             }
         obs[2 + ax] = dV * s;
+    }
+    if (d->nl_gauge && d->n_atoms > 0 && d->n_proj > 0) {
+        /* dv_nl/dA_x = -i [(r - R)_x, v_nl(A)], so
+         * <psi|dv_nl/dA_x|psi> = sum_ai D_ai 2 Re(i conj(P_ai) Q^x_ai) */
+        const int64_t np = (int64_t)d->n_atoms * d->n_proj;
+        cplx* P = (cplx*)work_proj;
+        cplx* Q = (cplx*)malloc(sizeof(cplx) * (size_t)np * no);
+        if (!Q) abort();
+        orc_project(d, A, psi_in, (double*)P);
+        for (int ax = 0; ax < 3; ++ax) {
+            orc_project_moment(d, A, ax, psi_in, (double*)Q);
+            double s = 0.0;
+            for (int64_t r = 0; r < np; ++r)
+                for (int o = 0; o < no; ++o)
+                    s += f[o] * d->D[r] * 2.0 * creal(I * conj(P[r * no + o]) * Q[r * no + o]);
+            obs[2 + ax] += s;
+        }
+        free(Q);
     }
 }
 
@@ -422,4 +491,4 @@ void orc_projector_values(const int32_t n[3], double h, int32_t n_atoms, const d
     }
 }
 
-int orc_abi_version(void) { return 1; }
+int orc_abi_version(void) { return 2; }

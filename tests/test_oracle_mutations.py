@@ -46,6 +46,14 @@ MUTANTS = [
      "cimag(in[g * no + o] * conj(gp[g * no + o]))"),
     ("energy without the nonlocal part", "orc_apply_h(d, A, psi_in, work, work_proj);\n    for (int64_t g = 0; g < ng; ++g)\n        for (int o = 0; o < no; ++o) {\n            cplx c = in[g * no + o];\n            nrm",
      "orc_apply_hloc(d, A, psi_in, work);\n    for (int64_t g = 0; g < ng; ++g)\n        for (int o = 0; o < no; ++o) {\n            cplx c = in[g * no + o];\n            nrm"),
+    ("velocity-gauge phase with the opposite sign", "return cos(th) - I * sin(th);", "return cos(th) + I * sin(th);"),
+    ("velocity-gauge phase missing from the scatter",
+     "out[(int64_t)d->idx[q] * no + o] += gauge_factor(d, A, a, d->idx[q]) * acc;",
+     "out[(int64_t)d->idx[q] * no + o] += acc;"),
+    ("velocity-gauge displacement without the minimum image", "dl[ax] = t - L * floor(t / L + 0.5);", "dl[ax] = t;"),
+    ("moment projection without the displacement", "wq *= dl[axis];", "wq *= 1.0;"),
+    ("moment projection on the wrong axis", "wq *= dl[axis];", "wq *= dl[(axis + 1) % 3];"),
+    ("nonlocal current with the opposite sign", "2.0 * creal(I * conj(P[r * no + o])", "2.0 * creal(-I * conj(P[r * no + o])"),
 ]
 
 

@@ -370,6 +370,105 @@ def test_translation_bit_exact_local():
 
 
 # ---------------------------------------------------------------------------
+# velocity-gauge projectors b e^{-iA.(r - R_a)} and their commutator current
+# ---------------------------------------------------------------------------
+
+def _gauge_domain(order=4, n=(6, 5, 7), h=0.55, n_orb=3, seed=5, atoms=None, gauge=True):
+    rng = np.random.default_rng(seed)
+    ng = n[0] * n[1] * n[2]
+    V = rng.uniform(-1, 0.5, ng)
+    L = np.array(n) * h
+    # one atom near a corner so that its sphere wraps on every axis
+    drawn = np.array([[0.3 * h, L[1] - 0.4 * h, 0.45 * h], rng.uniform(0, 1, 3) * L, rng.uniform(0, 1, 3) * L])
+    atoms = drawn if atoms is None else atoms
+    D = rng.uniform(-1, 1, (len(atoms), 4))
+    return oracle.Domain(n, h, n_orb, order, V, atoms, 4, r_c=0.7, r_cut=1.4, D=D, nl_gauge=gauge)
+
+
+def _grid_r(n, h):
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1) * h
+
+
+def test_gauge_projectors_equal_real_ones_at_zero_field():
+    d0 = _gauge_domain(gauge=False)
+    d1 = _gauge_domain(gauge=True)
+    psi = _rand_psi(d0.n_grid, 3, 1)
+    assert np.max(np.abs(d1.apply_h(psi, np.zeros(3)) - d0.apply_h(psi, np.zeros(3)))) == 0.0
+    assert np.max(np.abs(d1.project(psi, np.zeros(3)) - d0.project(psi))) == 0.0
+
+
+def test_gauge_covariance_at_reciprocal_lattice_field():
+    """For A = 2 pi m / L the phase U = e^{-iA.r} is periodic on the grid and
+    v_nl(A) = U v_nl(0) U^H exactly (the per-atom factor e^{iA.R_a} cancels
+    inside each projector): v_nl(A) U phi = U v_nl(0) phi for any phi, and
+    the nonlocal energy of U phi at A is that of phi at A = 0."""
+    n, h = (6, 5, 7), 0.55
+    dom = _gauge_domain(n=n, h=h)
+    L = np.array(n) * h
+    A = 2 * np.pi * np.array([1, -2, 1]) / L
+    U = np.exp(-1j * (_grid_r(n, h) @ A))[:, None]
+    phi = _rand_psi(dom.n_grid, 3, 2)
+    lhs = dom.apply_vnl(U * phi, A)
+    rhs = U * dom.apply_vnl(phi, np.zeros(3))
+    assert np.max(np.abs(lhs - rhs)) < 1e-13 * np.max(np.abs(rhs))
+    P_A = dom.project(U * phi, A)
+    P_0 = dom.project(phi, np.zeros(3))
+    e_A = np.einsum("ai,aio->", dom.D, np.abs(P_A) ** 2)
+    e_0 = np.einsum("ai,aio->", dom.D, np.abs(P_0) ** 2)
+    assert abs(e_A - e_0) < 1e-13 * abs(e_0)
+
+
+def test_gauge_translation_across_the_wrap():
+    """Shifting atoms and orbitals by whole grid vectors shifts v_nl(A) psi
+    at any A: the phase is taken from the minimum-image displacement, which
+    a shift carrying points across the box edge leaves unchanged."""
+    n, h = (6, 5, 7), 0.55
+    L = np.array(n) * h
+    s = np.array([4, -3, 5])
+    base = _gauge_domain(n=n, h=h)
+    moved = np.mod(base.atoms + s * h, L)
+    dom1 = _gauge_domain(n=n, h=h, atoms=moved)
+    psi = _rand_psi(base.n_grid, 3, 3)
+    A = np.array([0.31, -0.22, 0.17])
+
+    def shift(a):
+        return np.roll(a.reshape(n[2], n[1], n[0], -1), (s[2], s[1], s[0]), axis=(0, 1, 2)).reshape(base.n_grid, -1)
+
+    out0 = shift(base.apply_vnl(psi, A))
+    out1 = dom1.apply_vnl(shift(psi), A)
+    assert np.max(np.abs(out1 - out0)) < 1e-12 * np.max(np.abs(out0))
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_gauge_hamiltonian_hermitian(order):
+    dom = _gauge_domain(order=order, n=(5, 4, 6), h=0.6)
+    H = dom.dense_h(np.array([0.3, -0.15, 0.2]))
+    assert np.max(np.abs(H - H.conj().T)) < 1e-13 * np.max(np.abs(H))
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_gauge_current_is_derivative_of_energy(order):
+    """With velocity-gauge projectors E(A) is no longer quadratic in A; the
+    fourth-order central difference of E must match the current, which now
+    carries the nonlocal commutator part."""
+    dom = _gauge_domain(order=order)
+    psi = _rand_psi(dom.n_grid, 3, 9)
+    f = np.array([2.0, 2.0, 1.0])
+    A = np.array([0.21, -0.34, 0.16])
+    J = dom.observables(psi, A, f)[2:]
+    J_loc = _gauge_domain(order=order, gauge=False).observables(psi, A, f)[2:]
+    assert np.max(np.abs(J - J_loc)) > 1e-3 * np.max(np.abs(J))      # the nonlocal part is there
+    eps = 2e-3
+    for ax in range(3):
+        e = np.zeros(3)
+        e[ax] = eps
+        E = [dom.observables(psi, A + k * e, f)[1] for k in (-2, -1, 1, 2)]
+        dE = (E[0] - 8 * E[1] + 8 * E[2] - E[3]) / (12 * eps)
+        assert abs(dE - J[ax]) < 1e-9 * max(1.0, abs(J[ax]))
+
+
+# ---------------------------------------------------------------------------
 # re-orthonormalisation and the loss
 # ---------------------------------------------------------------------------
 
