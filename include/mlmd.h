@@ -160,6 +160,28 @@ MLMD_API mlmd_status mlmd_set_projectors(mlmd_domain_t dom, int32_t n_atoms, con
 MLMD_API mlmd_status mlmd_get_projector_lists(mlmd_domain_t dom, int64_t* off, int32_t* idx, size_t idx_cap,
                                      double* beta);
 
+/* Gauge of the nonlocal projectors (Eq. 3 with Sec. V.B.5's nonlocal
+ * energy and current).  MLMD_NL_GAUGE_REAL (the default): v_nl = sum
+ * |b_ai> D_ai <b_ai| with the real projectors of mlmd_set_projectors,
+ * independent of A.  MLMD_NL_GAUGE_VELOCITY: the minimal coupling of Eq. 3
+ * carried onto v_nl -- for uniform A, h(A) = e^{-iA.r} h(0) e^{iA.r}, so
+ * each projector becomes b~_ai(r) = e^{-i A.(r - R_a)} b_ai(r), with r - R_a
+ * the minimum-image displacement of the projector lists, re-evaluated at
+ * every step's A.  Then dh/dA_x gains the commutator -i[(r - R)_x, v_nl],
+ * and the current column of mlmd_propagate's observables (J = dE/dA) adds
+ *   sum_n f_n sum_ai D_ai 2 Re(i conj(<b~_ai|psi_n>) <(r - R_a)_x b~_ai|psi_n>),
+ * computed from three moment projections of the orbitals.  The
+ * velocity-gauge form runs on the per-point projection and scatter kernels
+ * (the TMA-staged and tensor-core nonlocal forms keep real projector tables
+ * and are not used while it is on).  mlmd_density_current's fields and J
+ * stay the local current density and its integral (the commutator term has
+ * no local density).  mlmd_propagate_adjoint returns MLMD_ERR_UNSUPPORTED
+ * for a domain with projectors in the velocity gauge.  May be called at any
+ * time; the setting survives mlmd_set_projectors.  MLMD_ERR_INVALID for an
+ * unknown gauge. */
+enum { MLMD_NL_GAUGE_REAL = 0, MLMD_NL_GAUGE_VELOCITY = 1 };
+MLMD_API mlmd_status mlmd_set_nonlocal_gauge(mlmd_domain_t dom, int32_t gauge);
+
 /* Propagate n_steps >= 0 Taylor-4 steps.  A: host double [n_steps][3], the
  * vector potential at each step's midpoint.  obs_out: NULL or host double
  * [n_steps][5]; row k holds, for the state before step k under h(A_k):

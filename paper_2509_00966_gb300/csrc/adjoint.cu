@@ -87,6 +87,8 @@ extern "C" mlmd_status mlmd_propagate_adjoint(mlmd_domain_t dom, int32_t n_steps
         MLMD_REQUIRE(d->desc.scheme == MLMD_SCHEME_FULL && d->desc.ortho_every == 0, MLMD_ERR_UNSUPPORTED,
                      "adjoint needs the full scheme without re-orthonormalisation");
         MLMD_REQUIRE(d->psi0_valid, MLMD_ERR_STATE, "no reference orbitals (call mlmd_set_orbitals)");
+        MLMD_REQUIRE(!gauge_on(*d), MLMD_ERR_UNSUPPORTED,
+                     "adjoint of the velocity-gauge projectors (dh/dA has the nonlocal commutator)");
         for (int i = 0; i < 3 * n_steps; ++i) MLMD_REQUIRE(std::isfinite(A[i]), MLMD_ERR_INVALID, "A not finite");
         Scratch S(*d);
         d->pa_psi = false;

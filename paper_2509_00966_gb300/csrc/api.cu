@@ -104,7 +104,7 @@ void Alloc::release_all() {
 // preceded by a projection pass over its input.
 void step_full(Domain& d, const double* Ak, double* obs_row) {
     const double dt = d.desc.dt;
-    if (d.nltc) {
+    if (nltc_on(d)) {
         // tensor-core nonlocal path: each stage is the local stencil kernel
         // (out = psi + gamma h_loc w), the scatter GEMM (out += gamma v_nl w
         // from P = <b|w>) and the projection GEMM of out for the next stage;
@@ -137,6 +137,8 @@ void step_full(Domain& d, const double* Ak, double* obs_row) {
     }
     const bool nl = d.has_nl();
     const bool fused = nl && tma_fused_nl(d);
+    const bool gauge = gauge_on(d);
+    if (gauge) launch_nl_phase(d, Ak);       // projector phases at this step's A
     if (fused && !d.pa_psi) launch_project(d, d.psi, d.Pa);
     const void* in = d.psi;
     void* outs[4] = {d.wa, d.wb, d.wa, d.psi};
@@ -158,7 +160,14 @@ void step_full(Domain& d, const double* Ak, double* obs_row) {
         bool done = false;
         const int nblk = launch_stage(d, a, &done);
         chain = fused && done;
-        if (s == 0 && obs_row) launch_obs_finish(d, d.obs_part, nblk, Ak, obs_row);
+        if (s == 0 && obs_row) {
+            launch_obs_finish(d, d.obs_part, nblk, Ak, obs_row);
+            if (gauge) {
+                // the nonlocal commutator current of psi (Pin[0] = <b~|psi>)
+                for (int ax = 0; ax < 3; ++ax) launch_project(d, d.psi, moment_buffer(d, ax), ax);
+                launch_nl_current(d, Pin[0], obs_row);
+            }
+        }
         in = outs[s];
     }
     d.pa_psi = chain;
@@ -275,6 +284,7 @@ double* ensure_dense(Domain& d, size_t doubles) {
 // out = h(A) in
 void apply_h(Domain& d, const void* in, void* out, const double* Ak, double* obs_row = nullptr) {
     const bool nl = d.has_nl();
+    if (gauge_on(d)) launch_nl_phase(d, Ak);
     if (nl) launch_project(d, in, d.Pa);
     StageArgs a;
     a.w = in;
@@ -286,7 +296,13 @@ void apply_h(Domain& d, const void* in, void* out, const double* Ak, double* obs
     a.gamma_im = 0.0;
     a.obs = obs_row ? d.obs_part : nullptr;
     const int nblk = launch_stage(d, a);
-    if (obs_row) launch_obs_finish(d, d.obs_part, nblk, Ak, obs_row);
+    if (obs_row) {
+        launch_obs_finish(d, d.obs_part, nblk, Ak, obs_row);
+        if (gauge_on(d)) {
+            for (int ax = 0; ax < 3; ++ax) launch_project(d, in, moment_buffer(d, ax), ax);
+            launch_nl_current(d, d.Pa, obs_row);
+        }
+    }
 }
 
 void reorth(Domain& d, int kind);
@@ -316,6 +332,7 @@ void apply_nnl(Domain& d) {
 void step_split(Domain& d, const double* Ak, double* obs_row) {
     d.pa_psi = false;
     if (obs_row) apply_h(d, d.psi, d.wb, Ak, obs_row);
+    else if (gauge_on(d)) launch_nl_phase(d, Ak);     // N_nl at this step's A
     if (d.has_nl()) apply_nnl(d);
     const double dt = d.desc.dt;
     const void* in = d.psi;
@@ -546,6 +563,18 @@ mlmd_status mlmd_set_projectors(mlmd_domain_t d, int32_t n_atoms, const double* 
             for (int i = 0; i < n_atoms * n_proj; ++i) MLMD_REQUIRE(std::isfinite(D[i]), MLMD_ERR_INVALID, "D not finite");
         }
         build_projectors(*d, n_atoms, pos, n_proj, r_c, r_cut, D);
+    });
+}
+
+mlmd_status mlmd_set_nonlocal_gauge(mlmd_domain_t d, int32_t gauge) {
+    return guarded(d, [&] {
+        MLMD_REQUIRE(gauge == MLMD_NL_GAUGE_REAL || gauge == MLMD_NL_GAUGE_VELOCITY, MLMD_ERR_INVALID,
+                     "unknown nonlocal gauge");
+        if (gauge == d->nl_gauge) return;
+        d->nl_gauge = gauge;
+        d->pa_psi = false;       // carried projections were taken with the other projectors
+        if (gauge == MLMD_NL_GAUGE_VELOCITY) gauge_build(*d);
+        else gauge_release(*d);
     });
 }
 

@@ -101,8 +101,8 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         // graph, so that the captured step is the steady-state one
         for (auto* d : b->doms) tma_autotune(*d, A_all);
         for (auto* d : b->doms)
-            if (d->has_nl() && !d->pa_psi && (d->nltc || tma_fused_nl(*d))) {
-                if (d->nltc) launch_nl_project_tc(*d, d->psi, d->Pa, false);
+            if (d->has_nl() && !d->pa_psi && (nltc_on(*d) || tma_fused_nl(*d))) {
+                if (nltc_on(*d)) launch_nl_project_tc(*d, d->psi, d->Pa, false);
                 else launch_project(*d, d->psi, d->Pa);
                 d->pa_psi = true;
             }

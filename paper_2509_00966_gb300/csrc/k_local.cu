@@ -169,12 +169,15 @@ GeoR<R> make_geo_r(const Domain& d) {
 // row covers point x = t / nv of line (y, z) and 16-byte vector j = t % nv.
 // ---------------------------------------------------------------------------
 // NLP: projectors per atom of the scatter-back (0: no nonlocal term, 4 or 8)
-template <typename R, int ORDER, int NLP, bool OBS, bool HAS_PSI>
+// GAUGE: velocity-gauge projectors; each entry's sum over its NLP projectors
+// is multiplied by the entry's phase ph[e] = e^{-i A.(r - R_a)}.
+template <typename R, int ORDER, int NLP, bool OBS, bool HAS_PSI, bool GAUGE>
 __global__ void __launch_bounds__(256) k_stage(GeoR<R> G, const R* __restrict__ w, const R* psi, R* out,
                                                const R* __restrict__ V, const R* __restrict__ f,
                                                const double* __restrict__ Ak,
                                                const int32_t* __restrict__ pstart,
                                                const int32_t* __restrict__ patom, const R* __restrict__ pbd,
+                                               const R* __restrict__ ph,
                                                const R* __restrict__ P, int n_proj, R gre, R gim,
                                                double* __restrict__ obs) {
     constexpr int NC = Vec<R>::NC;
@@ -237,13 +240,17 @@ __global__ void __launch_bounds__(256) k_stage(GeoR<R> G, const R* __restrict__ 
             const int e0 = pstart[g], e1 = pstart[g + 1];
             for (int e = e0; e < e1; e += EU) {
                 int a[EU];
-                R bd[EU][NLP];
+                R bd[EU][NLP], pc[EU], ps[EU];
                 Cx<R> pv[EU][NLP];
 #pragma unroll
                 for (int u = 0; u < EU; ++u) a[u] = e + u < e1 ? patom[e + u] : -1;
 #pragma unroll
                 for (int u = 0; u < EU; ++u)
                     if (a[u] >= 0) {
+                        if constexpr (GAUGE) {
+                            pc[u] = ph[2 * (int64_t)(e + u)];
+                            ps[u] = ph[2 * (int64_t)(e + u) + 1];
+                        }
 #pragma unroll
                         for (int i = 0; i < NLP; ++i) {
                             bd[u][i] = pbd[(int64_t)(e + u) * NLP + i];
@@ -253,13 +260,31 @@ __global__ void __launch_bounds__(256) k_stage(GeoR<R> G, const R* __restrict__ 
 #pragma unroll
                 for (int u = 0; u < EU; ++u)
                     if (a[u] >= 0) {
+                        if constexpr (GAUGE) {
+                            Cx<R> t;
 #pragma unroll
-                        for (int i = 0; i < NLP; ++i)
+                            for (int k = 0; k < NC; ++k) { t.re[k] = 0; t.im[k] = 0; }
+#pragma unroll
+                            for (int i = 0; i < NLP; ++i)
+#pragma unroll
+                                for (int k = 0; k < NC; ++k) {
+                                    t.re[k] += bd[u][i] * pv[u][i].re[k];
+                                    t.im[k] += bd[u][i] * pv[u][i].im[k];
+                                }
 #pragma unroll
                             for (int k = 0; k < NC; ++k) {
-                                hw.re[k] += bd[u][i] * pv[u][i].re[k];
-                                hw.im[k] += bd[u][i] * pv[u][i].im[k];
+                                hw.re[k] += pc[u] * t.re[k] - ps[u] * t.im[k];
+                                hw.im[k] += pc[u] * t.im[k] + ps[u] * t.re[k];
                             }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < NLP; ++i)
+#pragma unroll
+                                for (int k = 0; k < NC; ++k) {
+                                    hw.re[k] += bd[u][i] * pv[u][i].re[k];
+                                    hw.im[k] += bd[u][i] * pv[u][i].im[k];
+                                }
+                        }
                     }
             }
         }
@@ -310,20 +335,23 @@ void stage_dispatch(Domain& d, const StageArgs& a, dim3 grid) {
     const R* f = static_cast<const R*>(d.fR);
     const R* pbd = static_cast<const R*>(d.nl.pbd);
     const R* P = static_cast<const R*>(a.P);
-#define MLMD_STAGE(NLv, OBSv, HPv)                                                                   \
-    k_stage<R, ORDER, NLv, OBSv, HPv><<<grid, 256, 0, d.stream>>>(                                   \
-        G, w, psi, out, V, f, a.A, d.nl.pstart, d.nl.patom, pbd, P, d.nl.n_proj, (R)a.gamma_re,     \
+    const bool gauge = nl && gauge_on(d);
+    const R* ph = gauge ? static_cast<const R*>(d.nl.ph_pt) : nullptr;
+#define MLMD_STAGE(NLv, OBSv, HPv, GAv)                                                              \
+    k_stage<R, ORDER, NLv, OBSv, HPv, GAv><<<grid, 256, 0, d.stream>>>(                              \
+        G, w, psi, out, V, f, a.A, d.nl.pstart, d.nl.patom, pbd, ph, P, d.nl.n_proj, (R)a.gamma_re,  \
         (R)a.gamma_im, a.obs)
+#define MLMD_STAGE_NL(NLv, GAv)                                                                       \
+    if (obs) { if (hp) MLMD_STAGE(NLv, true, true, GAv); else MLMD_STAGE(NLv, true, false, GAv); }   \
+    else { if (hp) MLMD_STAGE(NLv, false, true, GAv); else MLMD_STAGE(NLv, false, false, GAv); }
     if (nl && d.nl.n_proj == 4) {
-        if (obs) { if (hp) MLMD_STAGE(4, true, true); else MLMD_STAGE(4, true, false); }
-        else { if (hp) MLMD_STAGE(4, false, true); else MLMD_STAGE(4, false, false); }
+        if (gauge) { MLMD_STAGE_NL(4, true) } else { MLMD_STAGE_NL(4, false) }
     } else if (nl) {
-        if (obs) { if (hp) MLMD_STAGE(8, true, true); else MLMD_STAGE(8, true, false); }
-        else { if (hp) MLMD_STAGE(8, false, true); else MLMD_STAGE(8, false, false); }
+        if (gauge) { MLMD_STAGE_NL(8, true) } else { MLMD_STAGE_NL(8, false) }
     } else {
-        if (obs) { if (hp) MLMD_STAGE(0, true, true); else MLMD_STAGE(0, true, false); }
-        else { if (hp) MLMD_STAGE(0, false, true); else MLMD_STAGE(0, false, false); }
+        MLMD_STAGE_NL(0, false)
     }
+#undef MLMD_STAGE_NL
 #undef MLMD_STAGE
 }
 
@@ -566,10 +594,12 @@ __global__ void __launch_bounds__(256) k_scale_orbitals(R* __restrict__ psi, int
     }
 }
 
-// out = in + i gamma_im * v_nl in   (v_nl from the projections P of in)
+// out = in + i gamma_im * v_nl in   (v_nl from the projections P of in;
+// ph: null, or the per-entry velocity-gauge phases e^{-i A.(r - R_a)})
 template <typename R>
 __global__ void __launch_bounds__(256) k_nl_apply(Geo G, const R* __restrict__ in, const int32_t* __restrict__ pstart,
                                                   const int32_t* __restrict__ patom, const R* __restrict__ pbd,
+                                                  const R* __restrict__ ph,
                                                   const R* __restrict__ P, int n_proj, R gim, R* out) {
     constexpr int NC = Vec<R>::NC;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -581,11 +611,25 @@ __global__ void __launch_bounds__(256) k_nl_apply(Geo G, const R* __restrict__ i
     for (int k = 0; k < NC; ++k) { acc.re[k] = 0; acc.im[k] = 0; }
     for (int e = pstart[g]; e < pstart[g + 1]; ++e) {
         const int a = patom[e];
+        Cx<R> t;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) { t.re[k] = 0; t.im[k] = 0; }
         for (int i = 0; i < n_proj; ++i) {
             const R bd = pbd[(int64_t)e * n_proj + i];
             const Cx<R> pv = ldg_c(rowp(P, (int64_t)a * n_proj + i, G.ld, j));
 #pragma unroll
-            for (int k = 0; k < NC; ++k) { acc.re[k] += bd * pv.re[k]; acc.im[k] += bd * pv.im[k]; }
+            for (int k = 0; k < NC; ++k) { t.re[k] += bd * pv.re[k]; t.im[k] += bd * pv.im[k]; }
+        }
+        if (ph) {
+            const R pc = ph[2 * (int64_t)e], ps = ph[2 * (int64_t)e + 1];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                acc.re[k] += pc * t.re[k] - ps * t.im[k];
+                acc.im[k] += pc * t.im[k] + ps * t.re[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) { acc.re[k] += t.re[k]; acc.im[k] += t.im[k]; }
         }
     }
     const Cx<R> c = ld_c(rowp(in, g, G.ld, j));
@@ -723,13 +767,15 @@ void launch_scale_orbitals(Domain& d, void* psi, const double* before, const dou
 void launch_nl_apply(Domain& d, const void* in, const void* P, void* out, double gamma_im) {
     const Geo G = make_geo(d);
     const int blocks = stage_blocks(d);
+    const void* ph = gauge_on(d) ? d.nl.ph_pt : nullptr;
     if (d.c64())
         k_nl_apply<float><<<blocks, 256, 0, d.stream>>>(G, (const float*)in, d.nl.pstart, d.nl.patom, (const float*)d.nl.pbd,
-                                                        (const float*)P, d.nl.n_proj, (float)gamma_im, (float*)out);
+                                                        (const float*)ph, (const float*)P, d.nl.n_proj, (float)gamma_im,
+                                                        (float*)out);
     else
         k_nl_apply<double><<<blocks, 256, 0, d.stream>>>(G, (const double*)in, d.nl.pstart, d.nl.patom,
-                                                         (const double*)d.nl.pbd, (const double*)P, d.nl.n_proj,
-                                                         gamma_im, (double*)out);
+                                                         (const double*)d.nl.pbd, (const double*)ph, (const double*)P,
+                                                         d.nl.n_proj, gamma_im, (double*)out);
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
 }

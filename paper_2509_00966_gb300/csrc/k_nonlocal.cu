@@ -224,6 +224,101 @@ __global__ void k_cast(const double* __restrict__ in, int64_t n, R* __restrict__
         out[i] = (R)in[i];
 }
 
+// ---- velocity-gauge tables --------------------------------------------------
+// Minimum-image displacement r - R_a of every list entry (one block per atom),
+// the same FP64 wrap as the list test, stored per axis in the working type.
+template <typename R>
+__global__ void __launch_bounds__(256) k_nl_disp(NLGeo G, const double* __restrict__ pos,
+                                                 const int64_t* __restrict__ off, const int32_t* __restrict__ idx,
+                                                 int64_t n_list, R* __restrict__ disp) {
+    const int a = blockIdx.x;
+    const double px = pos[3 * a], py = pos[3 * a + 1], pz = pos[3 * a + 2];
+    for (int64_t q = off[a] + threadIdx.x; q < off[a + 1]; q += blockDim.x) {
+        const int g = idx[q];
+        const int x = g % G.n[0], y = (g / G.n[0]) % G.n[1], z = g / (G.n[0] * G.n[1]);
+        disp[q] = (R)min_image(x, G.h, px, G.L[0]);
+        disp[n_list + q] = (R)min_image(y, G.h, py, G.L[1]);
+        disp[2 * n_list + q] = (R)min_image(z, G.h, pz, G.L[2]);
+    }
+}
+
+// pq[e] = the atom-list entry of per-point entry e: the position of point g
+// in its atom's list (ascending), found by bisection.
+__global__ void k_nl_pq(int64_t ng, const int32_t* __restrict__ pstart, const int32_t* __restrict__ patom,
+                        const int64_t* __restrict__ off, const int32_t* __restrict__ idx, int32_t* __restrict__ pq) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        for (int e = pstart[g]; e < pstart[g + 1]; ++e) {
+            const int a = patom[e];
+            int64_t lo = off[a], hi = off[a + 1] - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (idx[mid] < g) lo = mid + 1; else hi = mid;
+            }
+            pq[e] = (int32_t)lo;
+        }
+    }
+}
+
+// Phases of step k: theta = A_k . (r - R_a) in FP64;
+// ph_at[q] = e^{+i theta_q} (projection, atom-list order) and
+// ph_pt[e] = e^{-i theta_pq[e]} (scatter, per-point order).
+template <typename R>
+__global__ void __launch_bounds__(256) k_nl_phase(int64_t n_list, const R* __restrict__ disp,
+                                                  const int32_t* __restrict__ pq, const double* __restrict__ Ak,
+                                                  R* __restrict__ ph_at, R* __restrict__ ph_pt) {
+    const double A0 = Ak[0], A1 = Ak[1], A2 = Ak[2];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_list; q += (int64_t)gridDim.x * blockDim.x) {
+        double sn, cs;
+        const double th = A0 * (double)disp[q] + A1 * (double)disp[n_list + q] + A2 * (double)disp[2 * n_list + q];
+        sincos(th, &sn, &cs);
+        ph_at[2 * q] = (R)cs;
+        ph_at[2 * q + 1] = (R)sn;
+        const int64_t r = pq[q];
+        const double tr = A0 * (double)disp[r] + A1 * (double)disp[n_list + r] + A2 * (double)disp[2 * n_list + r];
+        sincos(tr, &sn, &cs);
+        ph_pt[2 * q] = (R)cs;
+        ph_pt[2 * q + 1] = (R)(-sn);
+    }
+}
+
+// Nonlocal commutator current (one block): row[2 + x] +=
+//   sum_(r,o) f_o D_r 2 Re(i conj(P_ro) Q^x_ro) = -2 sum f_o D_r (Pre Q^x_im - Pim Q^x_re)
+// over projector rows r = (atom, i) and orbitals o, summed in FP64.
+template <typename R>
+__global__ void __launch_bounds__(1024) k_nl_current(const R* __restrict__ P, const R* __restrict__ Q, int64_t qstride,
+                                                     const double* __restrict__ D, const double* __restrict__ f,
+                                                     int n_rows, int ld, int n_orb, double* __restrict__ row) {
+    double s[3] = {0.0, 0.0, 0.0};
+    const int64_t n = (int64_t)n_rows * n_orb;
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const int r = (int)(t / n_orb);
+        const int o = (int)(t - (int64_t)r * n_orb);
+        const int64_t e = ((int64_t)r * ld + o) * 2;
+        const double pr = (double)P[e], pi = (double)P[e + 1];
+        const double w = -2.0 * f[o] * D[r];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+            s[ax] += w * (pr * (double)Q[ax * qstride + e + 1] - pi * (double)Q[ax * qstride + e]);
+    }
+    __shared__ double red[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        for (int o = 16; o > 0; o >>= 1) s[ax] += __shfl_xor_sync(0xffffffffu, s[ax], o);
+        if (lane == 0) red[ax][warp] = s[ax];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            double t = lane < nw ? red[ax][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) row[2 + ax] += t;
+        }
+    }
+}
+
 // ---- projection -----------------------------------------------------------
 template <typename R> struct V16;
 template <> struct V16<float> { static constexpr int NC = 2; };
@@ -232,10 +327,13 @@ template <> struct V16<double> { static constexpr int NC = 1; };
 // Block (segment s, atom a, orbital chunk c): thread j owns one 16-byte
 // vector of the orbital row; loops over the segment's points and keeps the
 // NP projections in registers.  Pseg[s][a][i][o] = sum_{q in seg} beta[q][i] w[idx[q]][o].
-template <typename R, int NP>
+// GAUGE: each row is first multiplied by the complex phase ph[q] (and by the
+// displacement component mom[q] when mom is set).
+template <typename R, int NP, bool GAUGE>
 __global__ void __launch_bounds__(128) k_project(const R* __restrict__ w, int ld, int nv,
                                                  const int64_t* __restrict__ off,
                                                  const int32_t* __restrict__ idx, const R* __restrict__ beta,
+                                                 const R* __restrict__ ph, const R* __restrict__ mom,
                                                  int seg_len, int n_atoms, R* __restrict__ Pseg) {
     constexpr int NC = V16<R>::NC;
     const int s = blockIdx.x, a = blockIdx.y;
@@ -252,10 +350,19 @@ __global__ void __launch_bounds__(128) k_project(const R* __restrict__ w, int ld
         // flight before either is used
         for (int64_t q = q0; q < q1; q += 2) {
             const bool two = q + 1 < q1;
-            R v[2][2 * NC], b[2][NP];
+            R v[2][2 * NC], b[2][NP], pc[2], ps[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 if (u == 1 && !two) break;
+                if constexpr (GAUGE) {
+                    pc[u] = ph[2 * (q + u)];
+                    ps[u] = ph[2 * (q + u) + 1];
+                    if (mom) {
+                        const R m = mom[q + u];
+                        pc[u] *= m;
+                        ps[u] *= m;
+                    }
+                }
                 const R* row = w + ((int64_t)idx[q + u] * ld + (int64_t)j * NC) * 2;
                 if (NC == 2) {
                     const float4 t = __ldg(reinterpret_cast<const float4*>(row));
@@ -270,6 +377,14 @@ __global__ void __launch_bounds__(128) k_project(const R* __restrict__ w, int ld
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 if (u == 1 && !two) break;
+                if constexpr (GAUGE) {
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) {
+                        const R vr = v[u][2 * k], vi = v[u][2 * k + 1];
+                        v[u][2 * k] = pc[u] * vr - ps[u] * vi;
+                        v[u][2 * k + 1] = pc[u] * vi + ps[u] * vr;
+                    }
+                }
 #pragma unroll
                 for (int i = 0; i < NP; ++i)
 #pragma unroll
@@ -301,6 +416,7 @@ void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj
                       const double* D_host) {
     Nonlocal& nl = d.nl;
     // drop the previous tables
+    gauge_release(d);
     for (void* p : {(void*)nl.off, (void*)nl.idx, (void*)nl.beta64, nl.beta, (void*)nl.pstart, (void*)nl.patom,
                     nl.pbd, (void*)nl.D, d.Pa, d.Pb, d.Pseg})
         if (p) d.mem.put(p);
@@ -343,6 +459,7 @@ void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj
     nl.n_atoms = n_atoms;
     nl.n_proj = n_proj;
     nl.n_list = nl.h_off[n_atoms];
+    nl.h_pos.assign(pos_host, pos_host + 3 * (size_t)n_atoms);
     MLMD_REQUIRE(nl.n_list < (int64_t)INT32_MAX, MLMD_ERR_UNSUPPORTED, "projector lists too long");
     const int64_t nlist = std::max<int64_t>(nl.n_list, 1);
     nl.off = (int64_t*)d.mem.get(sizeof(int64_t) * (n_atoms + 1));
@@ -400,10 +517,84 @@ void build_projectors(Domain& d, int n_atoms, const double* pos_host, int n_proj
     d.mem.put(ent_q);
     tma_build_nl(d, D_host);
     nl_tc_build(d, pos_host, r_c, D_host);
+    if (d.nl_gauge == MLMD_NL_GAUGE_VELOCITY) gauge_build(d);
 }
 
-void launch_project(Domain& d, const void* w, void* P) {
+void gauge_release(Domain& d) {
+    Nonlocal& nl = d.nl;
+    for (void* p : {nl.disp, (void*)nl.pq, nl.ph_at, nl.ph_pt, nl.Qm})
+        if (p) d.mem.put(p);
+    nl.disp = nl.ph_at = nl.ph_pt = nl.Qm = nullptr;
+    nl.pq = nullptr;
+}
+
+void gauge_build(Domain& d) {
+    gauge_release(d);
+    if (!d.has_nl()) return;
+    Nonlocal& nl = d.nl;
+    const cudaStream_t st = d.stream;
+    NLGeo G{};
+    for (int ax = 0; ax < 3; ++ax) {
+        G.n[ax] = d.desc.n[ax];
+        G.L[ax] = (double)d.desc.n[ax] * d.desc.h;
+    }
+    G.h = d.desc.h;
+    const size_t rsz = d.c64() ? sizeof(float) : sizeof(double);
+    const int64_t nlist = std::max<int64_t>(nl.n_list, 1);
+    nl.disp = d.mem.get(rsz * 3 * nlist);
+    nl.pq = (int32_t*)d.mem.get(sizeof(int32_t) * nlist);
+    nl.ph_at = d.mem.get(rsz * 2 * nlist);
+    nl.ph_pt = d.mem.get(rsz * 2 * nlist);
+    nl.Qm = d.mem.get((size_t)3 * nl.n_atoms * nl.n_proj * d.ld * d.elem);
+    double* pos = (double*)d.mem.get(sizeof(double) * 3 * nl.n_atoms);
+    MLMD_CUDA(cudaMemcpyAsync(pos, nl.h_pos.data(), sizeof(double) * 3 * nl.n_atoms, cudaMemcpyHostToDevice, st));
+    if (d.c64()) k_nl_disp<float><<<nl.n_atoms, 256, 0, st>>>(G, pos, nl.off, nl.idx, nl.n_list, (float*)nl.disp);
+    else k_nl_disp<double><<<nl.n_atoms, 256, 0, st>>>(G, pos, nl.off, nl.idx, nl.n_list, (double*)nl.disp);
+    k_nl_pq<<<(int)std::min<int64_t>((d.ng + 255) / 256, 152 * 16), 256, 0, st>>>(d.ng, nl.pstart, nl.patom, nl.off,
+                                                                                   nl.idx, nl.pq);
+    d.launches += 2;
+    MLMD_CUDA(cudaGetLastError());
+    MLMD_CUDA(cudaStreamSynchronize(st));
+    d.mem.put(pos);
+}
+
+void launch_nl_phase(Domain& d, const double* Ak) {
     const Nonlocal& nl = d.nl;
+    MLMD_REQUIRE(nl.ph_at != nullptr, MLMD_ERR_STATE, "velocity-gauge tables missing");
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nl.n_list + 255) / 256, 152 * 8));
+    if (d.c64())
+        k_nl_phase<float><<<blocks, 256, 0, d.stream>>>(nl.n_list, (const float*)nl.disp, nl.pq, Ak,
+                                                        (float*)nl.ph_at, (float*)nl.ph_pt);
+    else
+        k_nl_phase<double><<<blocks, 256, 0, d.stream>>>(nl.n_list, (const double*)nl.disp, nl.pq, Ak,
+                                                         (double*)nl.ph_at, (double*)nl.ph_pt);
+    d.launches++;
+    MLMD_CUDA(cudaGetLastError());
+}
+
+void* moment_buffer(Domain& d, int ax) {
+    const size_t bytes = (size_t)d.nl.n_atoms * d.nl.n_proj * d.ld * d.elem;
+    return static_cast<char*>(d.nl.Qm) + bytes * ax;
+}
+
+void launch_nl_current(Domain& d, const void* P, double* obs_row) {
+    const Nonlocal& nl = d.nl;
+    const int n_rows = nl.n_atoms * nl.n_proj;
+    const int64_t qstride = (int64_t)n_rows * d.ld * 2;
+    if (d.c64())
+        k_nl_current<float><<<1, 1024, 0, d.stream>>>((const float*)P, (const float*)nl.Qm, qstride, nl.D, d.f, n_rows,
+                                                      d.ld, d.desc.n_orb, obs_row);
+    else
+        k_nl_current<double><<<1, 1024, 0, d.stream>>>((const double*)P, (const double*)nl.Qm, qstride, nl.D, d.f,
+                                                       n_rows, d.ld, d.desc.n_orb, obs_row);
+    d.launches++;
+    MLMD_CUDA(cudaGetLastError());
+}
+
+void launch_project(Domain& d, const void* w, void* P, int moment_axis) {
+    const Nonlocal& nl = d.nl;
+    const bool gauge = gauge_on(d);
+    MLMD_REQUIRE(gauge || moment_axis < 0, MLMD_ERR_STATE, "moment projection without velocity-gauge tables");
     const int nv = d.c64() ? d.ld / 2 : d.ld;
     const int bx = std::min(nv, 128);
     dim3 grid(nl.n_seg, nl.n_atoms, (nv + bx - 1) / bx);
@@ -411,23 +602,28 @@ void launch_project(Domain& d, const void* w, void* P) {
     const double dV = d.desc.h * d.desc.h * d.desc.h;
     const int rb = (int)std::min<int64_t>((n_real + 255) / 256, 152 * 8);
     ProfScope ps(d.prof, MLMD_KERNEL_PROJECT, d.stream);
-    if (d.c64()) {
-        if (nl.n_proj == 4)
-            k_project<float, 4><<<grid, bx, 0, d.stream>>>((const float*)w, d.ld, nv, nl.off, nl.idx, (const float*)nl.beta,
-                                                           nl.seg_len, nl.n_atoms, (float*)d.Pseg);
-        else
-            k_project<float, 8><<<grid, bx, 0, d.stream>>>((const float*)w, d.ld, nv, nl.off, nl.idx, (const float*)nl.beta,
-                                                           nl.seg_len, nl.n_atoms, (float*)d.Pseg);
-        k_project_reduce<float><<<rb, 256, 0, d.stream>>>((const float*)d.Pseg, nl.n_seg, n_real, (float)dV, (float*)P);
-    } else {
-        if (nl.n_proj == 4)
-            k_project<double, 4><<<grid, bx, 0, d.stream>>>((const double*)w, d.ld, nv, nl.off, nl.idx,
-                                                            (const double*)nl.beta, nl.seg_len, nl.n_atoms, (double*)d.Pseg);
-        else
-            k_project<double, 8><<<grid, bx, 0, d.stream>>>((const double*)w, d.ld, nv, nl.off, nl.idx,
-                                                            (const double*)nl.beta, nl.seg_len, nl.n_atoms, (double*)d.Pseg);
-        k_project_reduce<double><<<rb, 256, 0, d.stream>>>((const double*)d.Pseg, nl.n_seg, n_real, dV, (double*)P);
-    }
+    auto run = [&](auto zero) {
+        using R = decltype(zero);
+        const R* ph = static_cast<const R*>(nl.ph_at);
+        const R* mom = moment_axis >= 0 ? static_cast<const R*>(nl.disp) + (int64_t)moment_axis * nl.n_list : nullptr;
+        const R* beta = static_cast<const R*>(nl.beta);
+        R* seg = static_cast<R*>(d.Pseg);
+        const R* wr = static_cast<const R*>(w);
+        if (nl.n_proj == 4) {
+            if (gauge) k_project<R, 4, true><<<grid, bx, 0, d.stream>>>(wr, d.ld, nv, nl.off, nl.idx, beta, ph, mom,
+                                                                        nl.seg_len, nl.n_atoms, seg);
+            else k_project<R, 4, false><<<grid, bx, 0, d.stream>>>(wr, d.ld, nv, nl.off, nl.idx, beta, nullptr, nullptr,
+                                                                   nl.seg_len, nl.n_atoms, seg);
+        } else {
+            if (gauge) k_project<R, 8, true><<<grid, bx, 0, d.stream>>>(wr, d.ld, nv, nl.off, nl.idx, beta, ph, mom,
+                                                                        nl.seg_len, nl.n_atoms, seg);
+            else k_project<R, 8, false><<<grid, bx, 0, d.stream>>>(wr, d.ld, nv, nl.off, nl.idx, beta, nullptr, nullptr,
+                                                                   nl.seg_len, nl.n_atoms, seg);
+        }
+        k_project_reduce<R><<<rb, 256, 0, d.stream>>>(seg, nl.n_seg, n_real, (R)dV, static_cast<R*>(P));
+    };
+    if (d.c64()) run(0.0f);
+    else run(0.0);
     d.launches += 2;
     MLMD_CUDA(cudaGetLastError());
 }

@@ -1193,7 +1193,9 @@ void tma_build_nl(Domain& d, const double* D_host) {
     t.nl_ok = true;
 }
 
-bool tma_fused_nl(const Domain& d) { return d.tma && d.tma->ok && d.has_nl() && d.tma->nl_ok; }
+bool tma_fused_nl(const Domain& d) {
+    return d.tma && d.tma->ok && d.has_nl() && d.tma->nl_ok && !gauge_on(d);
+}
 
 int tma_blocks(const Domain& d) {
     if (!d.tma || !d.tma->ok) return 0;
@@ -1204,7 +1206,9 @@ bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done) {
     if (proj_done) *proj_done = false;
     if (!d.tma || !d.tma->ok) return false;
     const bool nl = d.has_nl() && a.P != nullptr;
-    if (nl && !d.tma->nl_ok) return false;
+    // the fused scatter holds real projector tables: velocity-gauge
+    // projectors take the per-point kernel
+    if (nl && (!d.tma->nl_ok || gauge_on(d))) return false;
     const bool proj = nl && a.P_out != nullptr;
     const TmaState& t = *d.tma;
     const TmaMaps m = maps_for(d, a.w);
@@ -1234,8 +1238,8 @@ void tma_autotune(Domain& d, const double* Ak) {
     TmaState& t = *d.tma;
     t.tuned = true;
     // tensor-core nonlocal domains run the stage kernel for the local part only
-    const bool nl = d.has_nl() && !d.nltc;
-    if (nl && !t.nl_ok) return;
+    const bool nl = d.has_nl() && !nltc_on(d);
+    if (nl && (!t.nl_ok || gauge_on(d))) return;
     // MLMD_STAGE_TILE="vp,tpp" (e.g. "8,4") fixes the shape instead, for
     // reproducible profiles; ignored unless it names a valid shape here
     if (const char* fix = std::getenv("MLMD_STAGE_TILE")) {

@@ -88,8 +88,16 @@ struct Nonlocal {
     void* pbd = nullptr;           // [n_list][n_proj] beta * D (working real type)
     double* D = nullptr;           // [n_atoms][n_proj]
     std::vector<int64_t> h_off;    // host copy of off
+    std::vector<double> h_pos;     // host copy of the atom positions [n_atoms][3]
     int n_seg = 0;                 // projection segments per atom
     int seg_len = 0;
+    // velocity-gauge tables (present while the domain's nonlocal gauge is
+    // MLMD_NL_GAUGE_VELOCITY)
+    void* disp = nullptr;          // [3][n_list] minimum-image displacement r - R_a (working real type)
+    int32_t* pq = nullptr;         // [n_list] atom-list entry of each per-point entry
+    void* ph_at = nullptr;         // [n_list] complex e^{+i A.(r - R_a)}, atom-list order (projection)
+    void* ph_pt = nullptr;         // [n_list] complex e^{-i A.(r - R_a)}, per-point order (scatter)
+    void* Qm = nullptr;            // [3][n_atoms][n_proj][ld] complex moment projections
 };
 
 // CUDA-event timing of selected kernel kinds (enabled by mlmd_profile_enable).
@@ -156,6 +164,7 @@ struct Domain {
     Profiler prof;
     TmaState* tma = nullptr;
     NlTc* nltc = nullptr;          // tensor-core nonlocal tables (dense-projector domains), or null
+    int nl_gauge = MLMD_NL_GAUGE_REAL;   // projector gauge (mlmd_set_nonlocal_gauge)
     double nl_rc = 0.0;            // projector width r_c of the current projectors
     int* err_flag = nullptr;       // device word raised by a kernel whose bounded wait expired
     mlmd_status latched = MLMD_OK;
@@ -164,6 +173,12 @@ struct Domain {
     bool c64() const { return desc.precision == MLMD_C64; }
     bool has_nl() const { return nl.n_atoms > 0 && nl.n_proj > 0; }
 };
+
+// The velocity-gauge projectors are in use (they run on the per-point
+// projection and scatter kernels).
+inline bool gauge_on(const Domain& d) { return d.nl_gauge == MLMD_NL_GAUGE_VELOCITY && d.has_nl(); }
+// The tensor-core nonlocal path is in use (real projectors only).
+inline bool nltc_on(const Domain& d) { return d.nltc != nullptr && d.nl_gauge == MLMD_NL_GAUGE_REAL; }
 
 // ---------------------------------------------------------------------------
 // kernels (launch wrappers count launches into dom.launches)
@@ -212,7 +227,19 @@ void tma_autotune(Domain& d, const double* Ak);
 int tma_chunk_bytes(const Domain& d);
 
 // P[a][i][o] = dV sum_q beta[q][i] w[idx[q]][o]
-void launch_project(Domain& d, const void* w, void* P);
+// P = <b|w> (dV included); with the velocity-gauge projectors <b~|w> at the
+// phases of the last launch_nl_phase, and for moment_axis >= 0 the moment
+// projection <(r - R_a)_axis b~|w>.
+void launch_project(Domain& d, const void* w, void* P, int moment_axis = -1);
+// Velocity-gauge tables: build (lists present) / drop; per-step phases at A_k.
+void gauge_build(Domain& d);
+void gauge_release(Domain& d);
+void launch_nl_phase(Domain& d, const double* Ak);
+// Moment projection buffer of axis ax (velocity gauge).
+void* moment_buffer(Domain& d, int ax);
+// obs_row[2 + x] += the nonlocal commutator current from P = <b~|psi> and
+// the moment projections in Qm (velocity gauge).
+void launch_nl_current(Domain& d, const void* P, double* obs_row);
 
 // Tensor-core nonlocal path (k_nl_tc.cu) for complex64 domains whose
 // projector spheres cover each grid point many times: brick tables built

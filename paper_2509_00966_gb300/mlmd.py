@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmlmd.so")
 C128, C64 = 0, 1
 GEMM = {"fp32": 0, "bf16": 1, "bf16x2": 2, "bf16x3": 3, "fp16": 4}
 SCHEME = {"full": 0, "split": 1}
+NL_GAUGE = {"real": 0, "velocity": 1}
 ORTHO = {"chol": 0, "lowdin": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error", 4: "numeric failure",
           5: "device wait timed out", 6: "invalid state", 7: "unsupported"}
@@ -60,6 +61,7 @@ _SIGS = {
     "mlmd_set_projectors": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_double,
                                            ctypes.c_double, _P]),
     "mlmd_get_projector_lists": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P]),
+    "mlmd_set_nonlocal_gauge": (ctypes.c_int, [_P, ctypes.c_int32]),
     "mlmd_propagate": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "mlmd_density_current": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32]),
     "mlmd_overlap": (ctypes.c_int, [_P, _P]),
@@ -190,6 +192,11 @@ def set_projectors(h, pos, n_proj, r_c, r_cut, D):
     D = _f64(D).reshape(na, -1) if na else np.zeros((0, max(n_proj, 1)))
     _check(lib().mlmd_set_projectors(h, na, ctypes.c_void_p(pos.ctypes.data), int(n_proj), float(r_c), float(r_cut),
                                      ctypes.c_void_p(D.ctypes.data)), h)
+
+
+def set_nonlocal_gauge(h, gauge):
+    """'real' (A-independent projectors) or 'velocity' (b e^{-iA.(r-R_a)})."""
+    _check(lib().mlmd_set_nonlocal_gauge(h, NL_GAUGE[gauge]), h)
 
 
 def projector_list_length(h, n_atoms):
@@ -437,6 +444,9 @@ class Domain:
         set_projectors(self.handle, pos, n_proj, r_c, r_cut, D)
         self.n_atoms = int(np.asarray(pos).reshape(-1, 3).shape[0])
         self.n_proj = int(n_proj) if self.n_atoms else 0
+
+    def set_nonlocal_gauge(self, gauge):
+        set_nonlocal_gauge(self.handle, gauge)
 
     def projector_lists(self):
         return get_projector_lists(self.handle, self.n_atoms, self.n_proj)
