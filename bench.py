@@ -56,12 +56,12 @@ STAGE_SRC = os.path.join(ROOT, "paper_2509_00966_gb300", "csrc", "k_stage_tma.cu
 # reports no traffic.  Per orbital*gridpoint, so that a capture on fewer
 # orbitals scales to the benchmark's orbital count.
 STAGE_TRAFFIC = {
-    # (306.4 + 190.5) + (562.7 + 197.7) + (563.3 + 196.4) + (540.8 + 186.7) MB over
+    # (306.4 + 190.5) + (562.5 + 197.4) + (563.2 + 196.4) + (540.9 + 186.6) MB over
     # the four launches, 48^3 x 256 orbitals
-    "c1": {"src_sha16": "3e6b07a9dbcfb0ce", "bytes_per_unit": 686.1e6 / (48 ** 3 * 256)},
-    # (766.3 + 502.0) + (1378.9 + 505.3) + (1379.4 + 509.1) + (1331.6 + 494.8) MB over
+    "c1": {"src_sha16": "180cba3cef9163c4", "bytes_per_unit": 686.0e6 / (48 ** 3 * 256)},
+    # (763.6 + 502.3) + (1375.8 + 505.6) + (1378.0 + 509.1) + (1327.9 + 494.5) MB over
     # the four launches, the c2 grid and projectors on 256 of its 1024 orbitals
-    "c2": {"src_sha16": "3e6b07a9dbcfb0ce", "bytes_per_unit": 1716.6e6 / (64 ** 3 * 256)},
+    "c2": {"src_sha16": "180cba3cef9163c4", "bytes_per_unit": 1714.2e6 / (64 ** 3 * 256)},
 }
 
 
@@ -97,6 +97,11 @@ def _args():
     p.add_argument("--stage-case", nargs=4, metavar=("CFG", "N_ORB", "QD_STEPS", "REPS"),
                    help="run only stage launches of workload CFG (c1 or c2) on N_ORB orbitals, REPS propagate "
                         "calls of QD_STEPS steps (a small case for ncu captures)")
+    p.add_argument("--sweep-case", nargs=4, metavar=("CFG", "N_ORB", "QD_STEPS", "REPS"),
+                   help="time the one-sweep local Taylor-4 against the four staged passes on a "
+                        "projector-free domain of config CFG's grid")
+    p.add_argument("--gauge-case", nargs=4, metavar=("CFG", "N_ORB", "QD_STEPS", "REPS"),
+                   help="time workload CFG on N_ORB orbitals with real and with velocity-gauge projectors")
     p.add_argument("--nl-case", nargs=4, metavar=("N", "N_ORB", "QD_STEPS", "REPS"),
                    help="one domain of the batched workload's kind (N^3 grid, h = 0.35, round(N^3/64) atoms x 4 "
                         "projectors): REPS propagate calls of QD_STEPS steps; per-kernel times")
@@ -725,6 +730,78 @@ def run_stage_case(args):
     d.close()
 
 
+# Real flops of one h_loc application per complex value (4th-order stencil):
+# neighbour sums 20, Laplacian 10, gradients 30, A.grad 10, diagonal 7; and
+# of one Taylor term (complex multiply-add) 8.
+SWEEP_FLOPS_PER_UNIT = {4: 4 * (77 + 8), 2: 4 * (41 + 8)}
+SMS, FP32_LANES = 152, 128
+
+
+def run_sweep_case(args):
+    """The one-sweep local Taylor-4 against the staged form on config CFG's
+    grid without projectors: N_ORB orbitals, REPS propagate calls of QD_STEPS
+    steps each, timed with CUDA events; orbital-gridpoint-steps per second
+    for both and the sweep's FP32 rate against the ALU peak."""
+    import torch
+    from paper_2509_00966_gb300 import build, inputs, mlmd
+    build.build()
+    torch.cuda.set_device(0)
+    cfg, no, qd, reps = args.sweep_case[0], int(args.sweep_case[1]), int(args.sweep_case[2]), int(args.sweep_case[3])
+    spec = inputs.config(cfg, n_orb=no)
+    V = inputs.gaussian_wells(spec.n, spec.h, spec.wells, spec.well_depth, spec.well_width)
+    A = spec.A[:qd]
+    out = {"case": f"{cfg} grid {spec.n} x {no} orbitals ({spec.precision}), no projectors, {qd} steps per call"}
+    for mode in ("sweep", "staged"):
+        os.environ["MLMD_SWEEP"] = "1" if mode == "sweep" else "0"
+        d = mlmd.Domain(spec.n, spec.h, no, spec.fd_order, spec.precision, "fp32", "full", spec.dt, 0)
+        d.set_potential(V)
+        d.set_orbitals(_device_orbitals(spec.n_grid, no, spec.dV, spec.seed,
+                                        torch.complex64 if spec.precision == "c64" else torch.complex128))
+        d.propagate(A, obs=False)
+        mlmd.profile_enable(d.handle, True)
+        ms, _ = _timed(lambda: d.propagate(A, obs=False), reps=reps)
+        t, c = mlmd.profile_read(d.handle, "stage")
+        units = spec.n_grid * no * qd
+        out[mode] = {"ms_per_step": ms / qd, "units_per_s": units / (ms * 1e-3),
+                     "stage_launches_per_step": c / max(reps * qd, 1), "stage_us_per_launch": 1e3 * t / max(c, 1)}
+        d.close()
+    os.environ.pop("MLMD_SWEEP", None)
+    fl = SWEEP_FLOPS_PER_UNIT[spec.fd_order] * out["sweep"]["units_per_s"]
+    out["sweep"]["flops_per_unit"] = SWEEP_FLOPS_PER_UNIT[spec.fd_order]
+    out["sweep"]["tflops"] = fl / 1e12
+    out["sweep"]["alu_peak_tflops_at_2070mhz"] = SMS * FP32_LANES * 2 * 2070e6 / 1e12
+    out["sweep"]["hbm_gbs_at_16B_per_unit"] = 2 * (8 if spec.precision == "c64" else 16) * out["sweep"]["units_per_s"] / 1e9
+    out["speedup"] = out["sweep"]["units_per_s"] / out["staged"]["units_per_s"]
+    print(json.dumps(out), flush=True)
+
+
+def run_gauge_case(args):
+    """Workload CFG (grid, atoms, projectors) on N_ORB orbitals: propagate
+    with observables every step, real projectors against velocity-gauge
+    projectors (per-step phases, per-point projection and scatter kernels,
+    three moment projections per step for the commutator current)."""
+    import torch
+    from paper_2509_00966_gb300 import build, inputs, mlmd
+    build.build()
+    torch.cuda.set_device(0)
+    cfg, no, qd, reps = args.gauge_case[0], int(args.gauge_case[1]), int(args.gauge_case[2]), int(args.gauge_case[3])
+    spec = inputs.config(cfg, n_orb=no)
+    V = inputs.gaussian_wells(spec.n, spec.h, spec.wells, spec.well_depth, spec.well_width)
+    A = spec.A[:qd]
+    out = {"case": f"{cfg} on {no} orbitals, {qd} steps per call with observables"}
+    for gauge in ("real", "velocity"):
+        d = mlmd.Domain.from_spec(spec, V=V, ortho_every=0)
+        d.set_nonlocal_gauge(gauge)
+        d.set_orbitals(_device_orbitals(spec.n_grid, no, spec.dV, spec.seed, torch.complex64))
+        d.propagate(A)
+        ms, obs = _timed(lambda: d.propagate(A), reps=reps)
+        units = spec.n_grid * no * qd
+        out[gauge] = {"ms_per_step": ms / qd, "units_per_s": units / (ms * 1e-3), "J_last": [float(v) for v in obs[-1, 2:]]}
+        d.close()
+    out["velocity_over_real_time"] = out["velocity"]["ms_per_step"] / out["real"]["ms_per_step"]
+    print(json.dumps(out), flush=True)
+
+
 def run_nl_case(args):
     """One c3-kind domain (dense projector spheres, tensor-core nonlocal
     path): per-kernel mean launch times of the stage, scatter and projection
@@ -905,6 +982,10 @@ def main():
         run_suite(args)
     elif args.stage_case:
         run_stage_case(args)
+    elif args.sweep_case:
+        run_sweep_case(args)
+    elif args.gauge_case:
+        run_gauge_case(args)
     elif args.nl_case:
         run_nl_case(args)
     else:

@@ -136,6 +136,13 @@ void step_full(Domain& d, const double* Ak, double* obs_row) {
         return;
     }
     const bool nl = d.has_nl();
+    if (!nl && sweep_on(d)) {
+        // no nonlocal term: all four Taylor terms in one sweep over psi
+        const int nblk = launch_sweep(d, d.psi, Ak, obs_row ? d.obs_part : nullptr);
+        if (obs_row) launch_obs_finish(d, d.obs_part, nblk, Ak, obs_row);
+        d.pa_psi = false;
+        return;
+    }
     const bool fused = nl && tma_fused_nl(d);
     const bool gauge = gauge_on(d);
     if (gauge) launch_nl_phase(d, Ak);       // projector phases at this step's A
@@ -334,6 +341,12 @@ void step_split(Domain& d, const double* Ak, double* obs_row) {
     if (obs_row) apply_h(d, d.psi, d.wb, Ak, obs_row);
     else if (gauge_on(d)) launch_nl_phase(d, Ak);     // N_nl at this step's A
     if (d.has_nl()) apply_nnl(d);
+    if (sweep_on(d)) {
+        // the local factor T4(h_loc) in one sweep
+        launch_sweep(d, d.psi, Ak, nullptr);
+        if (d.has_nl()) apply_nnl(d);
+        return;
+    }
     const double dt = d.desc.dt;
     const void* in = d.psi;
     void* outs[4] = {d.wa, d.wb, d.wa, d.psi};
@@ -465,6 +478,9 @@ mlmd_status mlmd_domain_create(const mlmd_domain_desc* desc, const mlmd_allocato
         d->err_flag = (int*)d->mem.get(sizeof(int));
         MLMD_CUDA(cudaMemsetAsync(d->err_flag, 0, sizeof(int), d->stream));
         tma_setup(*d);
+        sweep_setup(*d);
+        if (d->sweep.ok)
+            d->obs_blocks = std::max(d->obs_blocks, d->sweep.CX * d->sweep.CY * (d->ld / d->sweep.VPC));
         d->obs_part = (double*)d->mem.get(sizeof(double) * 5 * (size_t)std::max(d->obs_blocks, density_blocks(*d) * 2));
         MLMD_CUDA(cudaMemsetAsync(d->psi, 0, d->state_bytes, d->stream));
         MLMD_CUDA(cudaMemsetAsync(d->V, 0, rsz * d->ng, d->stream));
@@ -605,6 +621,7 @@ mlmd_status mlmd_propagate(mlmd_domain_t d, int32_t n_steps, const double* A, do
         MLMD_CUDA(cudaMemcpyAsync(d->A_dev, A, sizeof(double) * 3 * n_steps, cudaMemcpyHostToDevice, d->stream));
         if (obs_out) ensure_obs(*d, n_steps);
         tma_autotune(*d, d->A_dev);
+        sweep_autotune(*d, d->A_dev);
         for (int k = 0; k < n_steps; ++k) {
             const double* Ak = d->A_dev + 3 * k;
             double* row = obs_out ? d->obs_dev + 5 * k : nullptr;

@@ -99,7 +99,10 @@ mlmd_status mlmd_batch_propagate(mlmd_batch_t b, int32_t n_steps, const double* 
         MLMD_CUDA(cudaMemsetAsync(obs_cur, 0, sizeof(double) * 5 * nd, st));
         // tile choice and projections of the current orbitals, outside the
         // graph, so that the captured step is the steady-state one
-        for (auto* d : b->doms) tma_autotune(*d, A_all);
+        for (auto* d : b->doms) {
+            tma_autotune(*d, A_all);
+            sweep_autotune(*d, A_all);
+        }
         for (auto* d : b->doms)
             if (d->has_nl() && !d->pa_psi && (nltc_on(*d) || tma_fused_nl(*d))) {
                 if (nltc_on(*d)) launch_nl_project_tc(*d, d->psi, d->Pa, false);

@@ -1237,6 +1237,8 @@ void tma_autotune(Domain& d, const double* Ak) {
     if (!d.tma || !d.tma->ok || d.tma->tuned) return;
     TmaState& t = *d.tma;
     t.tuned = true;
+    // full-scheme steps without projectors run as one sweep (k_sweep.cu)
+    if (d.sweep.ok && d.sweep.use == 1 && !d.has_nl() && d.desc.scheme == MLMD_SCHEME_FULL) return;
     // tensor-core nonlocal domains run the stage kernel for the local part only
     const bool nl = d.has_nl() && !nltc_on(d);
     if (nl && (!t.nl_ok || gauge_on(d))) return;

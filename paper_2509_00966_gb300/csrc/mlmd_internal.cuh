@@ -70,6 +70,17 @@ struct Geo {
     double dV;
 };
 
+// Cluster tiling of the one-sweep local Taylor-4 kernel (k_sweep.cu): a
+// cluster of CX x CY CTAs covers a whole x-y plane for a chunk of VPC
+// orbitals, each CTA a TX x TY tile; ok = false when the domain does not fit.
+struct SweepPlan {
+    bool ok = false;
+    int CX = 0, CY = 0, TX = 0, TY = 0, VPC = 0, threads = 0;
+    size_t smem = 0;
+    int use = 0;                     // 1: sweep, -1: staged passes, 0: not yet timed
+    float t_sweep_ms = 0.f, t_staged_ms = 0.f;   // the timing that decided it
+};
+
 struct TmaState;   // TMA stage-kernel state (tensor maps, tiling), k_stage_tma.cu
 struct NlTc;       // brick tables of the tensor-core nonlocal path, k_nl_tc.cu
 
@@ -165,6 +176,7 @@ struct Domain {
     TmaState* tma = nullptr;
     NlTc* nltc = nullptr;          // tensor-core nonlocal tables (dense-projector domains), or null
     int nl_gauge = MLMD_NL_GAUGE_REAL;   // projector gauge (mlmd_set_nonlocal_gauge)
+    SweepPlan sweep;               // one-sweep local Taylor-4 tiling (ok = false: staged passes)
     double nl_rc = 0.0;            // projector width r_c of the current projectors
     int* err_flag = nullptr;       // device word raised by a kernel whose bounded wait expired
     mlmd_status latched = MLMD_OK;
@@ -240,6 +252,16 @@ void* moment_buffer(Domain& d, int ax);
 // obs_row[2 + x] += the nonlocal commutator current from P = <b~|psi> and
 // the moment projections in Qm (velocity gauge).
 void launch_nl_current(Domain& d, const void* P, double* obs_row);
+
+// One-sweep local Taylor-4 (k_sweep.cu): plan at domain creation; launch
+// buf <- T4(h_loc(A_k)) buf in place, with observable partials when obs_part
+// is set (returns their row count).
+SweepPlan plan_sweep(const Domain& d);
+void sweep_setup(Domain& d);
+int launch_sweep(Domain& d, void* buf, const double* Ak, double* obs_part);
+// First-propagate timing of the sweep against the staged passes (sets sweep.use).
+void sweep_autotune(Domain& d, const double* Ak);
+inline bool sweep_on(const Domain& d) { return d.sweep.ok && d.sweep.use == 1; }
 
 // Tensor-core nonlocal path (k_nl_tc.cu) for complex64 domains whose
 // projector spheres cover each grid point many times: brick tables built
