@@ -238,7 +238,7 @@ __device__ __forceinline__ size_t w3_off(int part, int nbricks, int brick, int x
 // projection's B operand).
 // ---------------------------------------------------------------------------
 template <int NP>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT + 32, 1)
     k_nl_scatter_tc(TcGeo G, const uint16_t* __restrict__ P3, int n_atoms, float* __restrict__ out,
                     uint16_t* __restrict__ w3, int nbricks, float gre, float gim, int stages, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(NT, 1)
     if (warp == 0) tmem_alloc(&tmem_base, tmem_cols(ncols));
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
-            mbar_init(&full[s], NT + 1);            // every thread, plus thread 0's expect_tx
+            mbar_init(&full[s], NT + 1);            // every generator thread, plus the issuer's expect_tx
             mbar_init(&empty[s], 1);
         }
         mbar_init(&done, 1);
@@ -272,67 +272,80 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    int issued = 0, consumed = 0;                   // thread 0: chunks whose copies were issued / landed
 
-    for (int c = 0; c < nchunks; ++c) {
-        const int st = c % stages;
-        unsigned char* sa = smem + (size_t)st * stage_bytes;
-        unsigned char* sb = sa + 3 * A_PART;
-        if (c >= stages && !mbar_wait_bounded(&empty[st], (uint32_t)((c / stages - 1) & 1))) {
-            abort_sh = 1;
-            break;
-        }
-        const int nv = min(4, na - c * 4);          // atoms of this chunk
-        if (tid == 0) {                              // B: the split D o P slabs of the chunk's atoms
-            mbar_expect_tx(&full[st], (uint32_t)nv * 3 * slab);
+    if (tid == NT) {
+        // issuer (warp 8, lane 0): bulk copies of D o P up to `stages` chunks
+        // ahead, then the MMAs of each chunk once its stage is full
+        int issued = 0, consumed = 0;               // chunks whose copies were issued / landed
+        for (int c = 0; c < nchunks && !abort_sh; ++c) {
+            for (; issued < nchunks && issued < c + stages; ++issued) {
+                const int cc = issued, st = cc % stages;
+                if (cc >= stages && !mbar_wait_bounded(&empty[st], (uint32_t)((cc / stages - 1) & 1))) {
+                    abort_sh = 1;
+                    break;
+                }
+                unsigned char* sb = smem + (size_t)st * stage_bytes + 3 * A_PART;
+                const int nv = min(4, na - cc * 4);
+                mbar_expect_tx(&full[st], (uint32_t)nv * 3 * slab);
 #pragma unroll 1
-            for (int j = 0; j < nv; ++j)
+                for (int j = 0; j < nv; ++j)
 #pragma unroll
-                for (int s = 0; s < 3; ++s)
-                    bulk_load(sb + (size_t)s * b_part + (size_t)j * slab, P3 + p3_off(s, n_atoms, S.id[c * 4 + j], ncols),
-                              slab, &full[st]);
-            issued = c + 1;
-        }
-        // K-octets of missing atoms (last chunk) are zero in B
-        for (int e = tid; e < (4 - nv) * 3 * ncols; e += NT) {
-            const int s = e / ((4 - nv) * ncols), r = e % ((4 - nv) * ncols);
-            *reinterpret_cast<uint4*>(sb + (size_t)s * b_part + (size_t)(nv + r / ncols) * slab + (size_t)(r % ncols) * 16) =
-                make_uint4(0, 0, 0, 0);
-        }
-        // A: B[p][r] for the 128 points x the chunk's 4 atoms; one unit = one
-        // point x one atom (its NP projectors, padded to 8); points fastest
-#pragma unroll 2
-        for (int it = tid; it < BP * 4; it += NT) {
-            const int p = it % BP, j = it / BP;
-            const int la = c * 4 + j;
-            int x, y, z;
-            const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
-            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (inside && la < na && mask_bit(S.mask[la], p)) {
-                float b[NP];
-                beta_at<NP>(G, S, la, x, y, z, b);
-#pragma unroll
-                for (int i = 0; i < NP; ++i) v[i] = b[i];
+                    for (int s = 0; s < 3; ++s)
+                        bulk_load(sb + (size_t)s * b_part + (size_t)j * slab,
+                                  P3 + p3_off(s, n_atoms, S.id[cc * 4 + j], ncols), slab, &full[st]);
             }
-            store_unit(sa, A_PART, unit_off(p, j), v);
-        }
-        fence_async_smem();
-        mbar_arrive(&full[st]);
-        if (tid == 0) {
+            if (abort_sh) break;
+            const int st = c % stages;
             if (!mbar_wait_bounded(&full[st], (uint32_t)((c / stages) & 1))) {
                 abort_sh = 1;
                 break;
             }
             consumed = c + 1;
             tc_fence_after();
-            issue_chunk(tmem, smem_u32(sa), smem_u32(sb), b_part, ncols, c == 0);
+            const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
+            issue_chunk(tmem, sa, sa + 3 * A_PART, b_part, ncols, c == 0);
             mma_commit(&empty[st]);
         }
-    }
-    if (tid == 0) {
         mma_commit(&done);                          // fires when every MMA issued above has completed
         for (int c = consumed; c < issued; ++c)     // after an abort: copies still in flight land first
             (void)mbar_wait_bounded(&full[c % stages], (uint32_t)((c / stages) & 1));
+    } else if (tid < NT) {
+        // generators (warps 0-7): the projector tile of each chunk
+        for (int c = 0; c < nchunks; ++c) {
+            const int st = c % stages;
+            unsigned char* sa = smem + (size_t)st * stage_bytes;
+            unsigned char* sb = sa + 3 * A_PART;
+            if (c >= stages && !mbar_wait_bounded(&empty[st], (uint32_t)((c / stages - 1) & 1))) {
+                abort_sh = 1;
+                break;
+            }
+            const int nv = min(4, na - c * 4);      // atoms of this chunk
+            // K-octets of missing atoms (last chunk) are zero in B
+            for (int e = tid; e < (4 - nv) * 3 * ncols; e += NT) {
+                const int s = e / ((4 - nv) * ncols), r = e % ((4 - nv) * ncols);
+                *reinterpret_cast<uint4*>(sb + (size_t)s * b_part + (size_t)(nv + r / ncols) * slab +
+                                          (size_t)(r % ncols) * 16) = make_uint4(0, 0, 0, 0);
+            }
+            // A: B[p][r] for the 128 points x the chunk's 4 atoms; one unit = one
+            // point x one atom (its NP projectors, padded to 8); points fastest
+#pragma unroll 2
+            for (int it = tid; it < BP * 4; it += NT) {
+                const int p = it % BP, j = it / BP;
+                const int la = c * 4 + j;
+                int x, y, z;
+                const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (inside && la < na && mask_bit(S.mask[la], p)) {
+                    float bv[NP];
+                    beta_at<NP>(G, S, la, x, y, z, bv);
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) v[i] = bv[i];
+                }
+                store_unit(sa, A_PART, unit_off(p, j), v);
+            }
+            fence_async_smem();
+            mbar_arrive(&full[st]);
+        }
     }
     const bool ok = mbar_wait_bounded(&done, 0);
     tc_fence_after();
@@ -349,7 +362,7 @@ __global__ void __launch_bounds__(NT, 1)
         // one 16-byte slab per (brick x-row, column), for the projection
         const int ldd = ncols + 4;                  // padded row (floats) against bank conflicts
         float* sD = reinterpret_cast<float*>(smem);
-        if (nchunks > 0) {
+        if (nchunks > 0 && tid < NT) {
             const int p = (warp & 3) * 32 + lane;
             const int half = ((ncols / 2 + 31) / 32) * 32;
             const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? ncols : min(half, ncols);
@@ -364,7 +377,7 @@ __global__ void __launch_bounds__(NT, 1)
             }
         }
         __syncthreads();
-        const int nq4 = ncols / 4, total = BP * nq4;
+        const int nq4 = ncols / 4, total = tid < NT ? BP * nq4 : 0;
         for (int it0 = tid; it0 < total; it0 += 4 * NT) {
             float4 o[4];
             float4* dst[4];
@@ -402,7 +415,7 @@ __global__ void __launch_bounds__(NT, 1)
         }
         __syncthreads();
         // split output: item = (x-row r, column n), columns fastest
-        for (int it = tid; it < 16 * ncols; it += NT) {
+        for (int it = tid; it < (tid < NT ? 16 * ncols : 0); it += NT) {
             const int r = it / ncols, n = it % ncols;
             float v[8];
 #pragma unroll
@@ -429,34 +442,43 @@ __global__ void __launch_bounds__(NT, 1)
 // x-row y = j -- and drained with vector atomics)
 // ---------------------------------------------------------------------------
 template <int NP>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT + 32, 1)
     k_nl_project_tc(TcGeo G, const uint16_t* __restrict__ w3, int nbricks, float* __restrict__ P, float dV, int stages,
                     int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    __shared__ __align__(8) uint64_t full[4], empty[4], done;
+    __shared__ __align__(8) uint64_t full[4], empty[4], done[2], drained[2];
     __shared__ __align__(8) uint64_t fin;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_sh;
     constexpr int APT = 128 / NP;                   // atoms per M-tile
+    constexpr int KCH = BP / KC;                    // K-chunks (z-planes) per tile
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int brick = blockIdx.x;
     const int bx = brick % G.nbx, by = (brick / G.nbx) % G.nby, bz = brick / (G.nbx * G.nby);
     const int a0 = G.bstart[brick], na = G.bstart[brick + 1] - a0;
     if (na == 0) return;
     const int ntiles = (na + APT - 1) / APT;
+    const int nch = ntiles * KCH;
     const int ncols = G.ld2;
     const uint32_t b_part = (uint32_t)ncols * KC * 2;
     const uint32_t stage_bytes = 3 * A_PART + 3 * b_part;
     const SAtoms<NP> S = stage_atoms<NP>(G, smem + (size_t)stages * stage_bytes, a0, na);
+    // two accumulators when they fit in tensor memory: tile t drains while
+    // tile t+1 accumulates
+    const uint32_t tcols = tmem_cols(ncols);
+    const int nbuf = 2 * tcols <= 512 ? 2 : 1;
 
-    if (warp == 0) tmem_alloc(&tmem_base, tmem_cols(ncols));
+    if (warp == 0) tmem_alloc(&tmem_base, tcols * (uint32_t)nbuf);
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
-            mbar_init(&full[s], NT + 1);            // every thread, plus thread 0's expect_tx
+            mbar_init(&full[s], NT + 1);            // every generator thread, plus the issuer's expect_tx
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&done[b], 1);
+            mbar_init(&drained[b], NT / 32);        // one arrival per generator warp
+        }
         mbar_init(&fin, 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -465,25 +487,87 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    int issued = 0, consumed = 0;                   // thread 0: chunks whose copies were issued / landed
 
-    for (int t = 0; t < ntiles; ++t) {
-        for (int kc = 0; kc < BP / KC; ++kc) {
-            const int c = t * (BP / KC) + kc;
-            const int st = c % stages;
-            unsigned char* sa = smem + (size_t)st * stage_bytes;
-            unsigned char* sb = sa + 3 * A_PART;
-            bool ok_e = true;
-            if (c >= stages) ok_e = mbar_wait_bounded(&empty[st], (uint32_t)((c / stages - 1) & 1));
-            if (!ok_e) abort_sh = 1;
-            if (ok_e) {
-                if (tid == 0) {                      // B: the split w of x-rows 4 kc .. 4 kc + 3, all columns
-                    mbar_expect_tx(&full[st], 3 * b_part);
+    if (tid == NT) {
+        // issuer: copies of the split output (the same four x-row groups for
+        // every tile) up to `stages` chunks ahead; the MMAs of a tile once
+        // its accumulator has been drained
+        int issued = 0, consumed = 0;
+        for (int c = 0; c < nch && !abort_sh; ++c) {
+            for (; issued < nch && issued < c + stages; ++issued) {
+                const int cc = issued, st = cc % stages, kc = cc % KCH;
+                if (cc >= stages && !mbar_wait_bounded(&empty[st], (uint32_t)((cc / stages - 1) & 1))) {
+                    abort_sh = 1;
+                    break;
+                }
+                unsigned char* sb = smem + (size_t)st * stage_bytes + 3 * A_PART;
+                mbar_expect_tx(&full[st], 3 * b_part);
 #pragma unroll
-                    for (int s = 0; s < 3; ++s)
-                        bulk_load(sb + (size_t)s * b_part, w3 + w3_off(s, nbricks, brick, kc * 4, ncols), b_part,
-                                  &full[st]);
-                    issued = c + 1;
+                for (int s = 0; s < 3; ++s)
+                    bulk_load(sb + (size_t)s * b_part, w3 + w3_off(s, nbricks, brick, kc * 4, ncols), b_part, &full[st]);
+            }
+            if (abort_sh) break;
+            const int t = c / KCH, kc = c % KCH, buf = t % nbuf, st = c % stages;
+            if (kc == 0 && t >= nbuf &&
+                !mbar_wait_bounded(&drained[buf], (uint32_t)((t / nbuf - 1) & 1))) {
+                abort_sh = 1;
+                break;
+            }
+            if (!mbar_wait_bounded(&full[st], (uint32_t)((c / stages) & 1))) {
+                abort_sh = 1;
+                break;
+            }
+            consumed = c + 1;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
+            issue_chunk(tmem + (uint32_t)buf * tcols, sa, sa + 3 * A_PART, b_part, ncols, kc == 0);
+            mma_commit(&empty[st]);
+            if (kc == KCH - 1) mma_commit(&done[buf]);
+        }
+        for (int c = consumed; c < issued; ++c)     // every copy lands before the memory is freed
+            (void)mbar_wait_bounded(&full[c % stages], (uint32_t)((c / stages) & 1));
+        mma_commit(&fin);
+        if (!mbar_wait_bounded(&fin, 0)) abort_sh = 1;
+    } else if (tid < NT) {
+        // generators (warps 0-7): B^T tiles; after tile t, the drain of tile t-1
+        const int r = (warp & 3) * 32 + lane;       // TMEM lane = row of the tile
+        const int half = ((ncols / 2 + 31) / 32) * 32;
+        const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? ncols : min(half, ncols);
+        auto drain = [&](int t) {
+            const int buf = t % nbuf;
+            const bool ok = mbar_wait_bounded(&done[buf], (uint32_t)((t / nbuf) & 1));
+            tc_fence_after();
+            if (!ok) { abort_sh = 1; return false; }
+            const int la = t * APT + r / NP;
+            float* dst = la < na ? P + ((size_t)S.id[la] * NP + r % NP) * ncols : nullptr;
+            for (int cb = c0; cb < c1; cb += 32) {
+                float v[32];
+                tmem_ld32(tmem + (uint32_t)buf * tcols + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
+                if (dst) {
+                    const int nw = min(32, c1 - cb);
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4)
+                        if (q < nw)
+                            atomicAdd(reinterpret_cast<float4*>(dst + cb + q),
+                                      make_float4(dV * v[q], dV * v[q + 1], dV * v[q + 2], dV * v[q + 3]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&drained[buf]);
+            return true;
+        };
+        bool live = true;
+        for (int t = 0; t < ntiles && live; ++t) {
+            if (nbuf == 1 && t > 0) live = drain(t - 1);       // one accumulator: drain before refilling it
+            for (int kc = 0; kc < KCH && live; ++kc) {
+                const int c = t * KCH + kc;
+                const int st = c % stages;
+                unsigned char* sa = smem + (size_t)st * stage_bytes;
+                if (c >= stages && !mbar_wait_bounded(&empty[st], (uint32_t)((c / stages - 1) & 1))) {
+                    abort_sh = 1;
+                    live = false;
+                    break;
                 }
                 // A: B^T[r][p] for the tile's 128 rows x the chunk's 32 points;
                 // one item = one atom x one brick x-row of 8 points (NP units)
@@ -512,61 +596,19 @@ __global__ void __launch_bounds__(NT, 1)
                         store_unit(sa, A_PART, unit_off(ra * NP + i, j), v);
                     }
                 }
+                fence_async_smem();
+                mbar_arrive(&full[st]);
             }
-            fence_async_smem();
-            mbar_arrive(&full[st]);         // always, so that the issuing thread's wait ends
-            if (tid == 0) {
-                if (!abort_sh && mbar_wait_bounded(&full[st], (uint32_t)((c / stages) & 1))) {
-                    consumed = c + 1;
-                    tc_fence_after();
-                    issue_chunk(tmem, smem_u32(sa), smem_u32(sb), b_part, ncols, kc == 0);
-                    mma_commit(&empty[st]);
-                } else {
-                    abort_sh = 1;
-                }
-                if (kc == BP / KC - 1) mma_commit(&done);   // one phase of `done` per tile
-            }
+            if (live && nbuf == 2 && t > 0) live = drain(t - 1);   // overlaps tile t's MMAs
         }
-        // drain the tile: lane = row (warp % 4), half of the columns per warp group
-        const bool ok = mbar_wait_bounded(&done, (uint32_t)(t & 1));
-        tc_fence_after();
-        if (!ok) abort_sh = 1;
-        __syncthreads();
-        if (abort_sh) break;                // the same decision in every thread
-        const int r = (warp & 3) * 32 + lane;
-        const int la = t * APT + r / NP;
-        const int half = ((ncols / 2 + 31) / 32) * 32;
-        const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? ncols : min(half, ncols);
-        float* dst = la < na ? P + ((size_t)S.id[la] * NP + r % NP) * ncols : nullptr;
-        for (int cb = c0; cb < c1; cb += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
-            if (dst) {
-                const int nw = min(32, c1 - cb);
-#pragma unroll
-                for (int q = 0; q < 32; q += 4)
-                    if (q < nw)
-                        atomicAdd(reinterpret_cast<float4*>(dst + cb + q),
-                                  make_float4(dV * v[q], dV * v[q + 1], dV * v[q + 2], dV * v[q + 3]));
-            }
-        }
-        tc_fence_before();
-        __syncthreads();                    // TMEM read before the next tile's MMAs overwrite it
-        tc_fence_after();
-    }
-    // every copy and MMA of this CTA has completed before its memory is freed
-    if (tid == 0) {
-        for (int c = consumed; c < issued; ++c)
-            (void)mbar_wait_bounded(&full[c % stages], (uint32_t)((c / stages) & 1));
-        mma_commit(&fin);
-        if (!mbar_wait_bounded(&fin, 0)) abort_sh = 1;
-        if (abort_sh) atomicExch(err, 1);
+        if (live) drain(ntiles - 1);
     }
     tc_fence_before();
     __syncthreads();
+    if (tid == 0 && abort_sh) atomicExch(err, 1);
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, tmem_cols(ncols));
+        tmem_dealloc(tmem, tcols * (uint32_t)nbuf);
     }
 }
 
@@ -813,7 +855,7 @@ void launch_nl_scatter_tc(Domain& d, const void* P, void* out, double gre, doubl
     const uint16_t* P3 = P == d.Pa ? t.P3a : t.P3b;
     ProfScope ps(d.prof, MLMD_KERNEL_SCATTER, d.stream);
     auto kern = np == 4 ? k_nl_scatter_tc<4> : k_nl_scatter_tc<8>;
-    kern<<<t.nbricks, NT, smem, d.stream>>>(G, P3, d.nl.n_atoms, (float*)out, t.w3, t.nbricks, (float)gre, (float)gim,
+    kern<<<t.nbricks, NT + 32, smem, d.stream>>>(G, P3, d.nl.n_atoms, (float*)out, t.w3, t.nbricks, (float)gre, (float)gim,
                                             stages, d.err_flag);
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
@@ -836,7 +878,7 @@ void launch_nl_project_tc(Domain& d, const void* w, void* P, bool w3_ready) {
     MLMD_CUDA(cudaMemsetAsync(P, 0, (size_t)d.nl.n_atoms * np * G.ld2 * sizeof(float), d.stream));
     const float dV = (float)(d.desc.h * d.desc.h * d.desc.h);
     auto kern = np == 4 ? k_nl_project_tc<4> : k_nl_project_tc<8>;
-    kern<<<t.nbricks, NT, smem, d.stream>>>(G, t.w3, t.nbricks, (float*)P, dV, stages, d.err_flag);
+    kern<<<t.nbricks, NT + 32, smem, d.stream>>>(G, t.w3, t.nbricks, (float*)P, dV, stages, d.err_flag);
     uint16_t* P3 = P == d.Pa ? t.P3a : t.P3b;
     const int64_t items = (int64_t)d.nl.n_atoms * G.ld2;
     const int blocks = (int)std::min<int64_t>((items + 255) / 256, 4096);
