@@ -56,12 +56,12 @@ STAGE_SRC = os.path.join(ROOT, "paper_2509_00966_gb300", "csrc", "k_stage_tma.cu
 # reports no traffic.  Per orbital*gridpoint, so that a capture on fewer
 # orbitals scales to the benchmark's orbital count.
 STAGE_TRAFFIC = {
-    # (306.4 + 190.5) + (562.5 + 197.4) + (563.2 + 196.4) + (540.9 + 186.6) MB over
+    # (306.0 + 190.4) + (561.9 + 197.7) + (563.3 + 196.3) + (540.4 + 186.8) MB over
     # the four launches, 48^3 x 256 orbitals
-    "c1": {"src_sha16": "180cba3cef9163c4", "bytes_per_unit": 686.0e6 / (48 ** 3 * 256)},
-    # (763.6 + 502.3) + (1375.8 + 505.6) + (1378.0 + 509.1) + (1327.9 + 494.5) MB over
+    "c1": {"src_sha16": "467869b53f9a01d2", "bytes_per_unit": 685.7e6 / (48 ** 3 * 256)},
+    # (764.0 + 502.3) + (1376.4 + 505.4) + (1377.5 + 509.3) + (1328.4 + 494.3) MB over
     # the four launches, the c2 grid and projectors on 256 of its 1024 orbitals
-    "c2": {"src_sha16": "180cba3cef9163c4", "bytes_per_unit": 1714.2e6 / (64 ** 3 * 256)},
+    "c2": {"src_sha16": "467869b53f9a01d2", "bytes_per_unit": 1714.4e6 / (64 ** 3 * 256)},
 }
 
 

@@ -777,21 +777,46 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
             for (int pi = 0; pi < NP; ++pi)
 #pragma unroll
                 for (int u = 0; u < NC; ++u) { acc[pi].re[u] = 0; acc[pi].im[u] = 0; }
-            for (int e = lo + eg; e < hi; e += EG) {
-                const int r = sRow[e];
-                // swizzled row start r*VP + (r mod 8): vector jj sits at that XOR jj
-                const int K = r * VP + (VP == 8 ? (r & 7) : 0);
-                Cv<R> w;
-                unpack(sW[K ^ jj], w);
-                R b[NP];
-                load_beta_s<R, NP>(sB + (int64_t)e * NP, b);
+            if constexpr (sizeof(R) == 4) {
+                // complex64: (re, im) pairs on packed f32x2 FMAs
+                float2 a2[NP][2];
 #pragma unroll
-                for (int pi = 0; pi < NP; ++pi)
+                for (int pi = 0; pi < NP; ++pi) a2[pi][0] = a2[pi][1] = make_float2(0.f, 0.f);
+                for (int e = lo + eg; e < hi; e += EG) {
+                    const int r = sRow[e];
+                    const int K = r * VP + (VP == 8 ? (r & 7) : 0);
+                    const float4 w4 = sW[K ^ jj];
+                    R b[NP];
+                    load_beta_s<R, NP>(sB + (int64_t)e * NP, b);
 #pragma unroll
-                    for (int u = 0; u < NC; ++u) {
-                        acc[pi].re[u] += b[pi] * w.re[u];
-                        acc[pi].im[u] += b[pi] * w.im[u];
+                    for (int pi = 0; pi < NP; ++pi) {
+                        const float2 bb = f2s((float)b[pi]);
+                        a2[pi][0] = f2fma(bb, lo2(w4), a2[pi][0]);
+                        a2[pi][1] = f2fma(bb, hi2(w4), a2[pi][1]);
                     }
+                }
+#pragma unroll
+                for (int pi = 0; pi < NP; ++pi) {
+                    acc[pi].re[0] = a2[pi][0].x; acc[pi].im[0] = a2[pi][0].y;
+                    acc[pi].re[NC - 1] = a2[pi][1].x; acc[pi].im[NC - 1] = a2[pi][1].y;
+                }
+            } else {
+                for (int e = lo + eg; e < hi; e += EG) {
+                    const int r = sRow[e];
+                    // swizzled row start r*VP + (r mod 8): vector jj sits at that XOR jj
+                    const int K = r * VP + (VP == 8 ? (r & 7) : 0);
+                    Cv<R> w;
+                    unpack(sW[K ^ jj], w);
+                    R b[NP];
+                    load_beta_s<R, NP>(sB + (int64_t)e * NP, b);
+#pragma unroll
+                    for (int pi = 0; pi < NP; ++pi)
+#pragma unroll
+                        for (int u = 0; u < NC; ++u) {
+                            acc[pi].re[u] += b[pi] * w.re[u];
+                            acc[pi].im[u] += b[pi] * w.im[u];
+                        }
+                }
             }
             // sum the entry groups (lanes jj, jj + VP, ...)
 #pragma unroll
