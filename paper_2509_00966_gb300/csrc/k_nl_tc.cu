@@ -59,6 +59,13 @@ struct NlTc {
     uint16_t* P3a = nullptr;      // split D o P of the projections in Pa: [3][n_atoms][2 ld][8] bf16
     uint16_t* P3b = nullptr;      // the same for Pb
     uint16_t* w3 = nullptr;       // split stage output: [3][nbricks][16][2 ld][8] bf16
+    // projector tiles built once per projector set (null: generated in every
+    // launch): one image of three bf16 parts per K-chunk, scatter chunks of
+    // brick b from soff[b], projection chunks (M-tile, plane) from poff[b]
+    unsigned char* As = nullptr;
+    unsigned char* Ap = nullptr;
+    int64_t* soff = nullptr;
+    int64_t* poff = nullptr;
 };
 
 namespace {
@@ -68,7 +75,8 @@ using namespace tc;
 constexpr int BX = 8, BY = 4, BZ = 4, BP = BX * BY * BZ;   // brick of 128 points
 constexpr int KC = 32;                                      // K elements per ring stage (4 K-octets)
 constexpr uint32_t A_PART = 128 * KC * 2;                   // one 16-bit part of a 128-row A tile
-constexpr int NT = 256;                                     // threads per CTA
+constexpr int NT = 256;                                     // generator threads per CTA
+constexpr uint32_t IMG = 3 * A_PART;                        // one K-chunk of A: its three bf16 parts
 
 struct TcGeo {
     int nx, ny, nz, nbx, nby;
@@ -82,6 +90,10 @@ struct TcGeo {
     const float4* apos;
     const float* anrm;
     const float* aD;
+    const unsigned char* As;      // projector tile images or null (NlTc)
+    const unsigned char* Ap;
+    const int64_t* soff;
+    const int64_t* poff;
 };
 
 // A tiles (128 rows x K = 32): byte offset of the 16-byte unit (row, K-octet
@@ -231,6 +243,87 @@ __device__ __forceinline__ size_t w3_off(int part, int nbricks, int brick, int x
     return ((((size_t)part * nbricks + brick) * 16 + xrow) * ncols) * 8;
 }
 
+// Projector tile of scatter chunk c (the brick's 128 points x the chunk's 4
+// atoms, one unit = one point x one atom's NP projectors padded to 8,
+// points fastest) into the three-part image at `dst` (a ring stage in
+// shared memory, or a device-memory image); threads tid, tid + nthr, ...
+template <int NP>
+__device__ __forceinline__ void gen_scatter_chunk(const TcGeo& G, const SAtoms<NP>& S, int bx, int by, int bz, int na,
+                                                  int c, unsigned char* dst, int tid, int nthr) {
+#pragma unroll 2
+    for (int it = tid; it < BP * 4; it += nthr) {
+        const int p = it % BP, j = it / BP;
+        const int la = c * 4 + j;
+        int x, y, z;
+        const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (inside && la < na && mask_bit(S.mask[la], p)) {
+            float bv[NP];
+            beta_at<NP>(G, S, la, x, y, z, bv);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) v[i] = bv[i];
+        }
+        store_unit(dst, A_PART, unit_off(p, j), v);
+    }
+}
+
+// Projector tile of projection chunk (M-tile t, brick z-plane kc): B^T for
+// the tile's 128 rows x the plane's 32 points; one item = one atom x one
+// x-row of 8 points (NP units).
+template <int NP>
+__device__ __forceinline__ void gen_project_chunk(const TcGeo& G, const SAtoms<NP>& S, int bx, int by, int bz, int na,
+                                                  int t, int kc, unsigned char* dst, int tid, int nthr) {
+    constexpr int APT = 128 / NP;
+    for (int it = tid; it < APT * 4; it += nthr) {
+        const int ra = it % APT, j = it / APT;
+        const int la = t * APT + ra;
+        float b[8][NP];
+        const uint4 mk = la < na ? S.mask[la] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int p = kc * KC + j * 8 + e;
+            int x, y, z;
+            const bool m = brick_point(G, bx, by, bz, p, x, y, z) && mask_bit(mk, p);
+            if (m) {
+                beta_at<NP>(G, S, la, x, y, z, b[e]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NP; ++i) b[e][i] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = b[e][i];
+            store_unit(dst, A_PART, unit_off(ra * NP + i, j), v);
+        }
+    }
+}
+
+// The images of both kernels' projector tiles for one brick (one CTA per
+// brick), built once per projector set: the same bytes the generators would
+// write into a ring stage in every launch.
+template <int NP>
+__global__ void __launch_bounds__(NT) k_nl_tiles(TcGeo G, unsigned char* __restrict__ As, unsigned char* __restrict__ Ap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int brick = blockIdx.x;
+    const int bx = brick % G.nbx, by = (brick / G.nbx) % G.nby, bz = brick / (G.nbx * G.nby);
+    const int a0 = G.bstart[brick], na = G.bstart[brick + 1] - a0;
+    if (na == 0) return;
+    const SAtoms<NP> S = stage_atoms<NP>(G, smem_raw, a0, na);
+    __syncthreads();
+    const int nchunks = (na + 3) / 4;
+    for (int c = 0; c < nchunks; ++c)
+        gen_scatter_chunk<NP>(G, S, bx, by, bz, na, c, As + ((size_t)G.soff[brick] + c) * IMG, threadIdx.x, NT);
+    constexpr int APT = 128 / NP;
+    const int ntiles = (na + APT - 1) / APT;
+    for (int t = 0; t < ntiles; ++t)
+        for (int kc = 0; kc < BP / KC; ++kc)
+            gen_project_chunk<NP>(G, S, bx, by, bz, na, t, kc,
+                                  Ap + ((size_t)G.poff[brick] + (size_t)t * (BP / KC) + kc) * IMG, threadIdx.x, NT);
+}
+
 // ---------------------------------------------------------------------------
 // scatter: out[p] += gamma sum_r B[p][r] D_r P[r]   (one CTA per brick)
 // K-octet j of chunk c is atom c*4 + j (its NP projectors, padded to 8).
@@ -284,9 +377,11 @@ __global__ void __launch_bounds__(NT + 32, 1)
                     abort_sh = 1;
                     break;
                 }
-                unsigned char* sb = smem + (size_t)st * stage_bytes + 3 * A_PART;
+                unsigned char* sa = smem + (size_t)st * stage_bytes;
+                unsigned char* sb = sa + 3 * A_PART;
                 const int nv = min(4, na - cc * 4);
-                mbar_expect_tx(&full[st], (uint32_t)nv * 3 * slab);
+                mbar_expect_tx(&full[st], (uint32_t)nv * 3 * slab + (G.As ? IMG : 0u));
+                if (G.As) bulk_load(sa, G.As + ((size_t)G.soff[brick] + cc) * IMG, IMG, &full[st]);
 #pragma unroll 1
                 for (int j = 0; j < nv; ++j)
 #pragma unroll
@@ -326,23 +421,8 @@ __global__ void __launch_bounds__(NT + 32, 1)
                 *reinterpret_cast<uint4*>(sb + (size_t)s * b_part + (size_t)(nv + r / ncols) * slab +
                                           (size_t)(r % ncols) * 16) = make_uint4(0, 0, 0, 0);
             }
-            // A: B[p][r] for the 128 points x the chunk's 4 atoms; one unit = one
-            // point x one atom (its NP projectors, padded to 8); points fastest
-#pragma unroll 2
-            for (int it = tid; it < BP * 4; it += NT) {
-                const int p = it % BP, j = it / BP;
-                const int la = c * 4 + j;
-                int x, y, z;
-                const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
-                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (inside && la < na && mask_bit(S.mask[la], p)) {
-                    float bv[NP];
-                    beta_at<NP>(G, S, la, x, y, z, bv);
-#pragma unroll
-                    for (int i = 0; i < NP; ++i) v[i] = bv[i];
-                }
-                store_unit(sa, A_PART, unit_off(p, j), v);
-            }
+            // A: the chunk's projector tile (copied by the issuer when prebuilt)
+            if (!G.As) gen_scatter_chunk<NP>(G, S, bx, by, bz, na, c, sa, tid, NT);
             fence_async_smem();
             mbar_arrive(&full[st]);
         }
@@ -500,8 +580,10 @@ __global__ void __launch_bounds__(NT + 32, 1)
                     abort_sh = 1;
                     break;
                 }
-                unsigned char* sb = smem + (size_t)st * stage_bytes + 3 * A_PART;
-                mbar_expect_tx(&full[st], 3 * b_part);
+                unsigned char* sa = smem + (size_t)st * stage_bytes;
+                unsigned char* sb = sa + 3 * A_PART;
+                mbar_expect_tx(&full[st], 3 * b_part + (G.Ap ? IMG : 0u));
+                if (G.Ap) bulk_load(sa, G.Ap + ((size_t)G.poff[brick] + cc) * IMG, IMG, &full[st]);
 #pragma unroll
                 for (int s = 0; s < 3; ++s)
                     bulk_load(sb + (size_t)s * b_part, w3 + w3_off(s, nbricks, brick, kc * 4, ncols), b_part, &full[st]);
@@ -569,33 +651,8 @@ __global__ void __launch_bounds__(NT + 32, 1)
                     live = false;
                     break;
                 }
-                // A: B^T[r][p] for the tile's 128 rows x the chunk's 32 points;
-                // one item = one atom x one brick x-row of 8 points (NP units)
-                for (int it = tid; it < APT * 4; it += NT) {
-                    const int ra = it % APT, j = it / APT;
-                    const int la = t * APT + ra;
-                    float b[8][NP];
-                    const uint4 mk = la < na ? S.mask[la] : make_uint4(0, 0, 0, 0);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int p = kc * KC + j * 8 + e;
-                        int x, y, z;
-                        const bool m = brick_point(G, bx, by, bz, p, x, y, z) && mask_bit(mk, p);
-                        if (m) {
-                            beta_at<NP>(G, S, la, x, y, z, b[e]);
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < NP; ++i) b[e][i] = 0.f;
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < NP; ++i) {
-                        float v[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) v[e] = b[e][i];
-                        store_unit(sa, A_PART, unit_off(ra * NP + i, j), v);
-                    }
-                }
+                // A: the chunk's projector tile (copied by the issuer when prebuilt)
+                if (!G.Ap) gen_project_chunk<NP>(G, S, bx, by, bz, na, t, kc, sa, tid, NT);
                 fence_async_smem();
                 mbar_arrive(&full[st]);
             }
@@ -720,6 +777,7 @@ TcGeo geo_for(const Domain& d) {
     widths(d.nl_rc, G.cexp, G.invrc);
     G.bstart = t.bstart; G.batom = t.batom; G.bmask = t.bmask;
     G.apos = t.apos; G.anrm = t.anrm; G.aD = t.aD;
+    G.As = t.As; G.Ap = t.Ap; G.soff = t.soff; G.poff = t.poff;
     return G;
 }
 
@@ -739,7 +797,7 @@ void nl_tc_release(Domain& d) {
     if (!d.nltc) return;
     NlTc& t = *d.nltc;
     for (void* p : {(void*)t.bstart, (void*)t.batom, (void*)t.bmask, (void*)t.apos, (void*)t.anrm, (void*)t.aD,
-                    (void*)t.P3a, (void*)t.P3b, (void*)t.w3})
+                    (void*)t.P3a, (void*)t.P3b, (void*)t.w3, (void*)t.As, (void*)t.Ap, (void*)t.soff, (void*)t.poff})
         if (p) d.mem.put(p);
     delete d.nltc;
     d.nltc = nullptr;
@@ -833,6 +891,36 @@ void nl_tc_build(Domain& d, const double* pos_host, double r_c, const double* D_
     const size_t smem = smem_for(2 * d.ld, t->max_atoms, np);
     ensure_dynamic_smem(reinterpret_cast<const void*>(np == 4 ? k_nl_scatter_tc<4> : k_nl_scatter_tc<8>), smem);
     ensure_dynamic_smem(reinterpret_cast<const void*>(np == 4 ? k_nl_project_tc<4> : k_nl_project_tc<8>), smem);
+
+    // projector tile images, built once here when they fit in half of the
+    // free device memory (MLMD_NL_TILES=0 keeps generating them per launch)
+    const char* te = std::getenv("MLMD_NL_TILES");
+    if (te && te[0] == '0') return;
+    const int apt = 128 / np;
+    std::vector<int64_t> soff(t->nbricks + 1, 0), poff(t->nbricks + 1, 0);
+    for (int b = 0; b < t->nbricks; ++b) {
+        const int nab = bstart[b + 1] - bstart[b];
+        soff[b + 1] = soff[b] + (nab + 3) / 4;
+        poff[b + 1] = poff[b] + (int64_t)((nab + apt - 1) / apt) * (BP / KC);
+    }
+    const size_t bytes_s = (size_t)soff[t->nbricks] * IMG, bytes_p = (size_t)poff[t->nbricks] * IMG;
+    size_t free_b = 0, total_b = 0;
+    MLMD_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (bytes_s + bytes_p == 0 || bytes_s + bytes_p > free_b / 2) return;
+    t->soff = (int64_t*)upload(soff.data(), sizeof(int64_t) * soff.size());
+    t->poff = (int64_t*)upload(poff.data(), sizeof(int64_t) * poff.size());
+    t->As = (unsigned char*)d.mem.get(std::max<size_t>(bytes_s, 16));
+    t->Ap = (unsigned char*)d.mem.get(std::max<size_t>(bytes_p, 16));
+    TcGeo G = geo_for(d);
+    G.As = G.Ap = nullptr;
+    const size_t asm_bytes = atom_bytes_for(t->max_atoms, np) + 16;
+    const void* bk = reinterpret_cast<const void*>(np == 4 ? k_nl_tiles<4> : k_nl_tiles<8>);
+    ensure_dynamic_smem(bk, asm_bytes);
+    if (np == 4) k_nl_tiles<4><<<t->nbricks, NT, asm_bytes, d.stream>>>(G, t->As, t->Ap);
+    else k_nl_tiles<8><<<t->nbricks, NT, asm_bytes, d.stream>>>(G, t->As, t->Ap);
+    d.launches++;
+    MLMD_CUDA(cudaGetLastError());
+    MLMD_CUDA(cudaStreamSynchronize(d.stream));
 }
 
 void launch_nl_energy(Domain& d, const void* P, double* row) {

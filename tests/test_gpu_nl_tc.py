@@ -93,3 +93,21 @@ def test_tensor_nonlocal_off_matches_on(monkeypatch):
     off, _, _, _, n_off = _run(spec, psi)
     assert n_on > 0 and n_off == 0
     assert np.max(np.abs(on - off)) <= 1e-5 and np.max(np.abs(off - ref)) <= 1e-5
+
+
+def test_prebuilt_tiles_match_generated(monkeypatch):
+    """The projector tiles built once per projector set are the bytes the
+    kernels would generate in every launch: orbitals and observables agree
+    with the images on and off to the rounding of the projection's
+    atomic accumulation (whose order varies from run to run)."""
+    spec = small_spec(precision="c64", n=(16, 8, 12), n_orb=37, n_proj=8, n_atoms=16, r_cut=2.2, steps=4)
+    psi = orbitals(spec)
+    monkeypatch.setenv("MLMD_NL_TC", "1")
+    a, oa, _, _, na_ = _run(spec, psi)
+    monkeypatch.setenv("MLMD_NL_TILES", "0")
+    b, ob, _, _, nb_ = _run(spec, psi)
+    assert na_ == nb_ == 4 * spec.n_steps
+    d_psi = np.max(np.abs(a - b))
+    d_obs = np.max(np.abs(oa - ob)) / np.max(np.abs(ob))
+    print(f"\n[errors] tiles on/off: psi={d_psi:.3e} obs={d_obs:.3e}", flush=True)
+    assert d_psi <= 1e-6 and d_obs <= 1e-6
