@@ -615,6 +615,14 @@ def run_c3(args, peaks, want_cpu):
             kcnt[kind] += c
         mlmd.profile_enable(dd.handle, False)
         n_list += dd.projector_list_length() * sp.n_orb
+    # the same Taylor step with the domains one at a time (no graph; each
+    # propagate returns its observables to the host), against the batched step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for dd, sp in zip(doms, specs):
+        dd.propagate(sp.A[:1], obs=True)
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t0) * 1e3
     # algorithmic nonlocal work of a Taylor step: per stage one projection and
     # one scatter, 4 real flops per (list entry, projector, orbital)
     nl_flops = 4 * 2 * 4 * 4.0 * n_list
@@ -654,6 +662,7 @@ def run_c3(args, peaks, want_cpu):
                          f"domain per bench step (one CUDA graph launch)"),
             "value": units * args.c3_steps / (t_ms * 1e-3), "unit": UNIT, "steps": args.c3_steps,
             "ms_per_step": t_ms / args.c3_steps, "units_per_step": units, "electrons": electrons,
+            "one_by_one_ms_per_step": seq_ms, "batched_speedup": seq_ms / (t_ms / args.c3_steps),
             "t2s_s_per_electron_step": (t_ms * 1e-3) / (args.c3_steps * electrons),
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -205,17 +205,14 @@ __global__ void k_offdiag_err(const double* __restrict__ T, int n, double* __res
 // ---- blocked FP64 complex Cholesky (panel width 32) ---------------------------
 constexpr int CB = 32;
 
-// Block column kb: every CTA loads the (already updated) 32 x 32 diagonal
-// block A11 and factors it in shared memory (all threads; FP64 issues slowly,
-// so no step runs on a single warp), then solves its own 32 panel rows
-// L21 L11^H = A21 column by column (right-looking: every thread updates its
-// share of the rows after each column).  CTA 0 stores L11 in Ld[kb], a side
-// array, so that no CTA overwrites A11 while another still reads it.
-// info > 0 marks a non-positive pivot.
-__global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int n, int kb, double* __restrict__ Ld,
-                                                    int* __restrict__ info) {
+// Block column kb, diagonal block only (one CTA): A11 = L11 L11^H, right-
+// looking in shared memory with all threads on each column's updates; L11
+// goes to Ld[kb] (the side array the panel solve and the triangular inverse
+// read, so that A11 in S stays untouched).  info > 0 marks a non-positive
+// pivot.
+__global__ void __launch_bounds__(256) k_chol_diag(const double* __restrict__ S, int n, int kb, double* __restrict__ Ld,
+                                                   int* __restrict__ info) {
     __shared__ double L[CB][CB + 1][2];
-    __shared__ double rows[CB][CB + 1][2];
     const int c0 = kb * CB;
     const int nb = min(CB, n - c0);
     for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
@@ -224,29 +221,22 @@ __global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int 
         L[i][j][0] = in ? S[((int64_t)(c0 + i) * n + c0 + j) * 2] : (i == j ? 1.0 : 0.0);
         L[i][j][1] = in ? S[((int64_t)(c0 + i) * n + c0 + j) * 2 + 1] : 0.0;
     }
-    // this CTA's panel rows r0 .. r0+31 below the diagonal block
-    const int r0 = c0 + nb + blockIdx.x * CB;
-    const int nr = r0 < n ? min(CB, n - r0) : 0;
-    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-        const int i = e / CB, j = e % CB;
-        const bool in = i < nr && j < nb;
-        rows[i][j][0] = in ? S[((int64_t)(r0 + i) * n + c0 + j) * 2] : 0.0;
-        rows[i][j][1] = in ? S[((int64_t)(r0 + i) * n + c0 + j) * 2 + 1] : 0.0;
-    }
+    __shared__ double inv_sh;
     __syncthreads();
-    // right-looking factorisation of the diagonal block
     for (int j = 0; j < nb; ++j) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0) {           // one FP64 square root and reciprocal per pivot
             double a = L[j][j][0];
             if (!(a > 0.0) || !isfinite(a)) { atomicCAS(info, 0, c0 + j + 1); a = 1.0; }
-            L[j][j][0] = sqrt(a);
+            const double r = sqrt(a);
+            L[j][j][0] = r;
             L[j][j][1] = 0.0;
+            inv_sh = 1.0 / r;
         }
         __syncthreads();
-        const double inv = 1.0 / L[j][j][0];
+        const double inv = inv_sh;
         for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) { L[i][j][0] *= inv; L[i][j][1] *= inv; }
         __syncthreads();
-        const int m = nb - j - 1;                         // trailing rows/cols of the block
+        const int m = nb - j - 1;
         for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
             const int i = j + 1 + e / m, k = j + 1 + e % m;
             if (k <= i) {
@@ -257,32 +247,50 @@ __global__ void __launch_bounds__(256) k_chol_panel(double* __restrict__ S, int 
         }
         __syncthreads();
     }
-    if (blockIdx.x == 0)
-        for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
-            const int i = e / CB, j = e % CB;
-            Ld[((int64_t)kb * CB * CB + e) * 2] = (j <= i) ? L[i][j][0] : 0.0;
-            Ld[((int64_t)kb * CB * CB + e) * 2 + 1] = (j <= i) ? L[i][j][1] : 0.0;
-        }
-    if (nr == 0) return;
-    // x L11^H = a, column by column: x_j = a_j / L_jj, then a_k -= x_j conj(L_kj), k > j
-    for (int j = 0; j < nb; ++j) {
-        const double dinv = 1.0 / L[j][j][0];
-        if (threadIdx.x < CB) { rows[threadIdx.x][j][0] *= dinv; rows[threadIdx.x][j][1] *= dinv; }
-        __syncthreads();
-        const int m = nb - j - 1;
-        for (int e = threadIdx.x; e < CB * m; e += blockDim.x) {
-            const int i = e / m, k = j + 1 + e % m;
-            const double xr = rows[i][j][0], xi = rows[i][j][1];
-            const double lr = L[k][j][0], li = -L[k][j][1];
-            rows[i][k][0] -= xr * lr - xi * li;
-            rows[i][k][1] -= xr * li + xi * lr;
-        }
-        __syncthreads();
+    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+        const int i = e / CB, j = e % CB;
+        Ld[((int64_t)kb * CB * CB + e) * 2] = (j <= i) ? L[i][j][0] : 0.0;
+        Ld[((int64_t)kb * CB * CB + e) * 2 + 1] = (j <= i) ? L[i][j][1] : 0.0;
     }
-    for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
-        const int i = e / nb, j = e % nb;
-        S[((int64_t)(r0 + i) * n + c0 + j) * 2] = rows[i][j][0];
-        S[((int64_t)(r0 + i) * n + c0 + j) * 2 + 1] = rows[i][j][1];
+}
+
+// Panel rows below the diagonal block: x L11^H = a for every row, one warp
+// per row with lane j holding column j: x_j = a_j / L_jj, then
+// a_k -= x_j conj(L_kj) for k > j (the same operations per element as the
+// right-looking block solve, without a block-wide barrier per column).
+__global__ void __launch_bounds__(256) k_chol_rows(double* __restrict__ S, int n, int kb, const double* __restrict__ Ld) {
+    __shared__ double L[CB][CB + 1][2];
+    __shared__ double dinv[CB];
+    const int c0 = kb * CB;
+    const int nb = min(CB, n - c0);
+    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+        const int i = e / CB, j = e % CB;
+        L[i][j][0] = Ld[((int64_t)kb * CB * CB + e) * 2];
+        L[i][j][1] = Ld[((int64_t)kb * CB * CB + e) * 2 + 1];
+    }
+    if (threadIdx.x < CB)
+        dinv[threadIdx.x] = 1.0 / Ld[((int64_t)kb * CB * CB + threadIdx.x * CB + threadIdx.x) * 2];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int row = c0 + nb + blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    if (row >= n) return;                           // whole warps leave together
+    double* a = S + ((int64_t)row * n + c0) * 2;
+    double ar = lane < nb ? a[lane * 2] : 0.0, ai = lane < nb ? a[lane * 2 + 1] : 0.0;
+    for (int j = 0; j < nb; ++j) {
+        if (lane == j) {
+            ar *= dinv[j];
+            ai *= dinv[j];
+        }
+        const double xr = __shfl_sync(0xffffffffu, ar, j), xi = __shfl_sync(0xffffffffu, ai, j);
+        if (lane > j && lane < nb) {
+            const double lr = L[lane][j][0], li = -L[lane][j][1];
+            ar -= xr * lr - xi * li;
+            ai -= xr * li + xi * lr;
+        }
+    }
+    if (lane < nb) {
+        a[lane * 2] = ar;
+        a[lane * 2 + 1] = ai;
     }
 }
 
@@ -576,8 +584,12 @@ void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info) {
     double* Ld = (double*)d.mem.get((size_t)nblk * CB * CB * 2 * sizeof(double));
     for (int kb = 0; kb < nblk; ++kb) {
         const int below = n - (kb * CB + std::min(CB, n - kb * CB));
-        k_chol_panel<<<std::max(1, (below + CB - 1) / CB), 256, 0, d.stream>>>(S, n, kb, Ld, d_info);
+        k_chol_diag<<<1, 256, 0, d.stream>>>(S, n, kb, Ld, d_info);
         d.launches++;
+        if (below > 0) {
+            k_chol_rows<<<(below + 7) / 8, 256, 0, d.stream>>>(S, n, kb, Ld);
+            d.launches++;
+        }
         if (below > 0) {
             const int t = (below + CB - 1) / CB;
             k_chol_trail<<<dim3(t, t), 256, 0, d.stream>>>(S, n, kb);

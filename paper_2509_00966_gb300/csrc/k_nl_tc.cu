@@ -434,63 +434,45 @@ __global__ void __launch_bounds__(NT + 32, 1)
     if (abort_sh) {
         if (tid == 0) atomicExch(err, 1);
     } else {
-        // epilogue through shared memory (the ring is free now): warp w copies
-        // TMEM lanes 32 (w % 4) .. +31 (points), one half of the columns, into
-        // a [point][column] array; all threads then add gamma D to out row by
-        // row with coalesced 16-byte accesses, keeping the new values in the
-        // array; last the array goes out transposed and split into bf16 parts,
-        // one 16-byte slab per (brick x-row, column), for the projection
+        // epilogue (the ring is free now): warp w reads TMEM lanes 32 (w % 4) ..
+        // +31 (one grid point per lane) over one half of the columns, adds
+        // gamma D to the point's output row with eight 16-byte loads in flight
+        // per lane, and keeps the new values in a [point][column] array for
+        // the split, transposed copy that the projection reads
         const int ldd = ncols + 4;                  // padded row (floats) against bank conflicts
         float* sD = reinterpret_cast<float*>(smem);
-        if (nchunks > 0 && tid < NT) {
+        if (tid < NT) {
             const int p = (warp & 3) * 32 + lane;
+            int x, y, z;
+            const bool inside = brick_point(G, bx, by, bz, p, x, y, z);
+            float* orow = inside ? out + ((size_t)x + (size_t)G.nx * ((size_t)y + (size_t)G.ny * z)) * ncols : nullptr;
             const int half = ((ncols / 2 + 31) / 32) * 32;
             const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? ncols : min(half, ncols);
             for (int cb = c0; cb < c1; cb += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
                 const int nw = min(32, c1 - cb);
+                float v[32];
+                if (nchunks > 0) {
+                    tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb, v);
+                } else {
 #pragma unroll
-                for (int q = 0; q < 32; q += 4)
-                    if (q < nw)
-                        *reinterpret_cast<float4*>(sD + p * ldd + cb + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-            }
-        }
-        __syncthreads();
-        const int nq4 = ncols / 4, total = tid < NT ? BP * nq4 : 0;
-        for (int it0 = tid; it0 < total; it0 += 4 * NT) {
-            float4 o[4];
-            float4* dst[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int it = it0 + u * NT;
-                dst[u] = nullptr;
-                o[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (it < total) {
-                    const int p = it / nq4, nq = it % nq4;
-                    int x, y, z;
-                    if (brick_point(G, bx, by, bz, p, x, y, z)) {
-                        dst[u] = reinterpret_cast<float4*>(
-                                     out + ((size_t)x + (size_t)G.nx * ((size_t)y + (size_t)G.ny * z)) * ncols) + nq;
-                        o[u] = *dst[u];
-                    }
+                    for (int q = 0; q < 32; ++q) v[q] = 0.f;
                 }
-            }
+                float4 o[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int it = it0 + u * NT;
-                if (it >= total) continue;
-                const int p = it / nq4, nq = it % nq4;
-                float4* sp = reinterpret_cast<float4*>(sD + p * ldd + 4 * nq);
-                if (dst[u] && nchunks > 0) {
-                    const float4 dv = *sp;
-                    o[u].x += gre * dv.x - gim * dv.y;
-                    o[u].y += gre * dv.y + gim * dv.x;
-                    o[u].z += gre * dv.z - gim * dv.w;
-                    o[u].w += gre * dv.w + gim * dv.z;
-                    *dst[u] = o[u];
+                for (int q = 0; q < 8; ++q)
+                    o[q] = (orow && 4 * q < nw) ? *reinterpret_cast<const float4*>(orow + cb + 4 * q)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (4 * q >= nw) continue;
+                    const float* d4 = v + 4 * q;
+                    o[q].x += gre * d4[0] - gim * d4[1];
+                    o[q].y += gre * d4[1] + gim * d4[0];
+                    o[q].z += gre * d4[2] - gim * d4[3];
+                    o[q].w += gre * d4[3] + gim * d4[2];
+                    if (orow) *reinterpret_cast<float4*>(orow + cb + 4 * q) = o[q];
+                    *reinterpret_cast<float4*>(sD + p * ldd + cb + 4 * q) = o[q];   // zero outside the grid
                 }
-                *sp = o[u];                          // the brick's output (zero outside the grid)
             }
         }
         __syncthreads();
