@@ -366,44 +366,57 @@ __global__ void __launch_bounds__(NT + 32, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
-    if (tid == NT) {
-        // issuer (warp 8, lane 0): bulk copies of D o P up to `stages` chunks
-        // ahead, then the MMAs of each chunk once its stage is full
+    if (warp == NT / 32) {
+        // issuer warp: lane 0 waits on the barriers and issues the MMAs; the
+        // bulk copies of a chunk (the tile image and the 3 x 4 D o P slabs)
+        // are spread over the lanes, up to `stages` chunks ahead
         int issued = 0, consumed = 0;               // chunks whose copies were issued / landed
-        for (int c = 0; c < nchunks && !abort_sh; ++c) {
+        bool stop = false;
+        for (int c = 0; c < nchunks && !stop; ++c) {
             for (; issued < nchunks && issued < c + stages; ++issued) {
                 const int cc = issued, st = cc % stages;
-                if (cc >= stages && !mbar_wait_bounded(&empty[st], (uint32_t)((cc / stages - 1) & 1))) {
-                    abort_sh = 1;
+                int ok = 1;
+                if (lane == 0 && cc >= stages) ok = mbar_wait_bounded(&empty[st], (uint32_t)((cc / stages - 1) & 1));
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    stop = true;
                     break;
                 }
                 unsigned char* sa = smem + (size_t)st * stage_bytes;
                 unsigned char* sb = sa + 3 * A_PART;
                 const int nv = min(4, na - cc * 4);
-                mbar_expect_tx(&full[st], (uint32_t)nv * 3 * slab + (G.As ? IMG : 0u));
-                if (G.As) bulk_load(sa, G.As + ((size_t)G.soff[brick] + cc) * IMG, IMG, &full[st]);
-#pragma unroll 1
-                for (int j = 0; j < nv; ++j)
-#pragma unroll
-                    for (int s = 0; s < 3; ++s)
-                        bulk_load(sb + (size_t)s * b_part + (size_t)j * slab,
-                                  P3 + p3_off(s, n_atoms, S.id[cc * 4 + j], ncols), slab, &full[st]);
+                if (lane == 0) mbar_expect_tx(&full[st], (uint32_t)nv * 3 * slab + (G.As ? IMG : 0u));
+                __syncwarp();
+                if (lane < nv * 3) {
+                    const int jj = lane / 3, s = lane % 3;
+                    bulk_load(sb + (size_t)s * b_part + (size_t)jj * slab,
+                              P3 + p3_off(s, n_atoms, S.id[cc * 4 + jj], ncols), slab, &full[st]);
+                }
+                if (G.As && lane == 31) bulk_load(sa, G.As + ((size_t)G.soff[brick] + cc) * IMG, IMG, &full[st]);
+                __syncwarp();
             }
-            if (abort_sh) break;
+            if (stop) break;
             const int st = c % stages;
-            if (!mbar_wait_bounded(&full[st], (uint32_t)((c / stages) & 1))) {
-                abort_sh = 1;
-                break;
+            int ok = 1;
+            if (lane == 0) {
+                ok = mbar_wait_bounded(&full[st], (uint32_t)((c / stages) & 1));
+                if (ok) {
+                    consumed = c + 1;
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
+                    issue_chunk(tmem, sa, sa + 3 * A_PART, b_part, ncols, c == 0);
+                    mma_commit(&empty[st]);
+                }
             }
-            consumed = c + 1;
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
-            issue_chunk(tmem, sa, sa + 3 * A_PART, b_part, ncols, c == 0);
-            mma_commit(&empty[st]);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) stop = true;
         }
-        mma_commit(&done);                          // fires when every MMA issued above has completed
-        for (int c = consumed; c < issued; ++c)     // after an abort: copies still in flight land first
-            (void)mbar_wait_bounded(&full[c % stages], (uint32_t)((c / stages) & 1));
+        if (lane == 0) {
+            if (stop) abort_sh = 1;
+            mma_commit(&done);                      // fires when every MMA issued above has completed
+            for (int c = consumed; c < issued; ++c) // after an abort: copies still in flight land first
+                (void)mbar_wait_bounded(&full[c % stages], (uint32_t)((c / stages) & 1));
+        }
     } else if (tid < NT) {
         // generators (warps 0-7): the projector tile of each chunk
         for (int c = 0; c < nchunks; ++c) {
