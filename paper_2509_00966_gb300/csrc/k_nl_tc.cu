@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(NT + 32, 1)
     if (warp == 0) tmem_alloc(&tmem_base, tmem_cols(ncols));
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
-            mbar_init(&full[s], NT + 1);            // every generator thread, plus the issuer's expect_tx
+            mbar_init(&full[s], G.As ? 1 : NT + 1);   // the issuer's expect_tx, plus every generator without images
             mbar_init(&empty[s], 1);
         }
         mbar_init(&done, 1);
@@ -393,6 +393,14 @@ __global__ void __launch_bounds__(NT + 32, 1)
                               P3 + p3_off(s, n_atoms, S.id[cc * 4 + jj], ncols), slab, &full[st]);
                 }
                 if (G.As && lane == 31) bulk_load(sa, G.As + ((size_t)G.soff[brick] + cc) * IMG, IMG, &full[st]);
+                if (G.As && nv < 4) {               // K-octets of missing atoms (last chunk) are zero in B
+                    for (int e = lane; e < (4 - nv) * 3 * ncols; e += 32) {
+                        const int s = e / ((4 - nv) * ncols), r = e % ((4 - nv) * ncols);
+                        *reinterpret_cast<uint4*>(sb + (size_t)s * b_part + (size_t)(nv + r / ncols) * slab +
+                                                  (size_t)(r % ncols) * 16) = make_uint4(0, 0, 0, 0);
+                    }
+                    fence_async_smem();
+                }
                 __syncwarp();
             }
             if (stop) break;
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(NT + 32, 1)
             for (int c = consumed; c < issued; ++c) // after an abort: copies still in flight land first
                 (void)mbar_wait_bounded(&full[c % stages], (uint32_t)((c / stages) & 1));
         }
-    } else if (tid < NT) {
+    } else if (tid < NT && !G.As) {
         // generators (warps 0-7): the projector tile of each chunk
         for (int c = 0; c < nchunks; ++c) {
             const int st = c % stages;
@@ -547,7 +555,7 @@ __global__ void __launch_bounds__(NT + 32, 1)
     if (warp == 0) tmem_alloc(&tmem_base, tcols * (uint32_t)nbuf);
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
-            mbar_init(&full[s], NT + 1);            // every generator thread, plus the issuer's expect_tx
+            mbar_init(&full[s], G.Ap ? 1 : NT + 1);   // the issuer's expect_tx, plus every generator without images
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -637,7 +645,7 @@ __global__ void __launch_bounds__(NT + 32, 1)
         bool live = true;
         for (int t = 0; t < ntiles && live; ++t) {
             if (nbuf == 1 && t > 0) live = drain(t - 1);       // one accumulator: drain before refilling it
-            for (int kc = 0; kc < KCH && live; ++kc) {
+            for (int kc = 0; kc < KCH && live && !G.Ap; ++kc) {   // (with images the issuer fills the stages alone)
                 const int c = t * KCH + kc;
                 const int st = c % stages;
                 unsigned char* sa = smem + (size_t)st * stage_bytes;

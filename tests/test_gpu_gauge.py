@@ -155,3 +155,27 @@ def test_gauge_adjoint_is_unsupported():
         d.propagate_adjoint(spec.A, ckpt_every=2)
     assert e.value.status == 7
     d.close()
+
+
+def test_gauge_on_dense_projector_domain():
+    """A domain of the batched workload's density (about 41 projector spheres
+    over every point) in the velocity gauge: the tensor-core nonlocal path
+    holds real projector tables, so the step falls back to the per-point
+    kernels with phases and still matches the oracle."""
+    from paper_2509_00966_gb300 import inputs, mlmd
+    spec = inputs.batched_specs(n_domains=2, n_steps=3, seed=11)[1]
+    d, V = gpu_domain(spec)
+    d.set_nonlocal_gauge("velocity")
+    psi = inputs.random_orbitals(spec.n_grid, spec.n_orb, spec.dV, 78)
+    d.set_orbitals(to_device(psi, "c64"))
+    mlmd.profile_enable(d.handle, True)
+    obs = d.propagate(spec.A)
+    n_scatter = mlmd.profile_read(d.handle, "scatter")[1]
+    out = to_numpy(d.get_orbitals())
+    d.close()
+    assert n_scatter == 0                     # no tensor-core scatter launches
+    ref, robs = oracle.propagate(_oracle_gauge(spec, V), psi, spec.A, spec.dt, np.full(spec.n_orb, 2.0))
+    err = np.max(np.abs(out - ref))
+    print(f"\n[errors] gauge dense domain N={spec.n[0]} x {spec.n_orb}: psi={err:.3e}", flush=True)
+    assert err <= 1e-5
+    _check_obs(obs, robs, 1e-6)
