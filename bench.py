@@ -80,7 +80,7 @@ def _args():
     p.add_argument("--c1-qd-steps", type=int, default=1000, help="Taylor steps per c1 benchmark step")
     p.add_argument("--c1-steps", type=int, default=5, help="timed c1 benchmark steps")
     p.add_argument("--c3-steps", type=int, default=10, help="timed c3 benchmark steps")
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=4)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU work of each oracle sample")
     p.add_argument("--ks", nargs=3, metavar=("N", "N_ORB", "MODE"),
@@ -492,6 +492,7 @@ def run_c2(args, peaks, ws, rank, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": _job_value(ws, units_step, e2e_s), "unit": UNIT,
+                "ms_per_call": [round(t * 1e3, 1) for t in e2e_t],
                 "h2d_bytes_per_step": int(spec.n_grid * spec.n_orb * 8 + C2_QD_PER_STEP * 3 * 8),
                 "d2h_bytes_per_step": int(spec.n_grid * spec.n_orb * 8 + C2_QD_PER_STEP * 5 * 8)},
         "gpu_launches": int(launches),

@@ -516,9 +516,22 @@ mlmd_status mlmd_set_orbitals(mlmd_domain_t d, const void* psi, int32_t on_devic
         MLMD_REQUIRE(psi != nullptr, MLMD_ERR_INVALID, "null orbitals");
         d->pa_psi = false;
         const size_t src_pitch = (size_t)d->desc.n_orb * d->elem, dst_pitch = (size_t)d->ld * d->elem;
-        MLMD_CUDA(cudaMemsetAsync(d->psi, 0, d->state_bytes, d->stream));
-        MLMD_CUDA(cudaMemcpy2DAsync(d->psi, dst_pitch, psi, src_pitch, src_pitch, (size_t)d->ng,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, d->stream));
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (src_pitch == dst_pitch) {
+            // no padding orbitals: the rows are contiguous, one flat copy
+            MLMD_CUDA(cudaMemcpyAsync(d->psi, psi, d->state_bytes, kind, d->stream));
+        } else {
+            MLMD_CUDA(cudaMemsetAsync(d->psi, 0, d->state_bytes, d->stream));     // padding orbitals stay zero
+            const void* src = psi;
+            if (!on_device) {
+                // from the host as one flat copy into the work buffer, then
+                // into the padded rows on the device
+                MLMD_CUDA(cudaMemcpyAsync(d->wa, psi, src_pitch * (size_t)d->ng, cudaMemcpyHostToDevice, d->stream));
+                src = d->wa;
+            }
+            MLMD_CUDA(cudaMemcpy2DAsync(d->psi, dst_pitch, src, src_pitch, src_pitch, (size_t)d->ng,
+                                        cudaMemcpyDeviceToDevice, d->stream));
+        }
         if (!d->psi0) d->psi0 = d->mem.get(d->state_bytes);
         MLMD_CUDA(cudaMemcpyAsync(d->psi0, d->psi, d->state_bytes, cudaMemcpyDeviceToDevice, d->stream));
         if (!on_device) MLMD_CUDA(cudaStreamSynchronize(d->stream));
@@ -531,8 +544,17 @@ mlmd_status mlmd_get_orbitals(mlmd_domain_t d, void* psi_out, int32_t on_device)
     return guarded(d, [&] {
         MLMD_REQUIRE(psi_out != nullptr, MLMD_ERR_INVALID, "null output");
         const size_t dst_pitch = (size_t)d->desc.n_orb * d->elem, src_pitch = (size_t)d->ld * d->elem;
-        MLMD_CUDA(cudaMemcpy2DAsync(psi_out, dst_pitch, d->psi, src_pitch, dst_pitch, (size_t)d->ng,
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, d->stream));
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (src_pitch == dst_pitch) {
+            MLMD_CUDA(cudaMemcpyAsync(psi_out, d->psi, d->state_bytes, kind, d->stream));
+        } else if (on_device) {
+            MLMD_CUDA(cudaMemcpy2DAsync(psi_out, dst_pitch, d->psi, src_pitch, dst_pitch, (size_t)d->ng, kind, d->stream));
+        } else {
+            // packed on the device into the work buffer, then one flat copy to the host
+            MLMD_CUDA(cudaMemcpy2DAsync(d->wa, dst_pitch, d->psi, src_pitch, dst_pitch, (size_t)d->ng,
+                                        cudaMemcpyDeviceToDevice, d->stream));
+            MLMD_CUDA(cudaMemcpyAsync(psi_out, d->wa, dst_pitch * (size_t)d->ng, cudaMemcpyDeviceToHost, d->stream));
+        }
         if (!on_device) MLMD_CUDA(cudaStreamSynchronize(d->stream));
     });
 }
