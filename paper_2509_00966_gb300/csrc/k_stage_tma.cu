@@ -46,6 +46,7 @@ struct TmaState {
     bool vp8_ok = false;      // the row splits into 128-byte chunks
     bool tuned = false;       // tile shape chosen by timing
     int zc = 0;               // planes per CTA
+    int zc_full = 0;          // planes per CTA without projectors (zc <= zc_full)
     int ncols = 0;            // tiles x z-chunks
     std::vector<TmaMaps> maps;
     // nonlocal tables of the fused path (device, owned by the domain's allocator)
@@ -73,6 +74,8 @@ struct TmaState {
 namespace {
 
 constexpr int TX = 8, TY = 8;
+// most z planes one CTA computes
+constexpr int kMaxZc = 32;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 template <typename R> struct V16;
@@ -161,9 +164,11 @@ template <int VP> struct Slot {
 };
 // Scatter entry blocks have a ring of their own: the block of computed plane
 // j is brought two planes ahead of its use into slot j % ESL.
-constexpr int ESL = 3;
-// psi's centre tiles (when they come by TMA) have a ring of PSL slots.
-constexpr int PSL = 3;
+constexpr int ESL = 2;
+// psi's centre tiles (when they come by TMA) have a ring of PSL slots.  One
+// plane of look-ahead for both is enough; the shared memory goes to a fifth
+// w slot instead (two planes of w in flight).
+constexpr int PSL = 2;
 
 // Vector (x+dx, y+dy) of the plane in slot s, one of dx, dy zero, |d| <= 2.
 template <int VP>
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     __shared__ __align__(8) uint64_t bars[NSLOT];
     __shared__ __align__(8) uint64_t ebars[ESL];
     __shared__ __align__(8) uint64_t pbars[PSL];
-    __shared__ int64_t soff[17];                    // entry-block offsets of the column's planes (zc <= 16)
+    __shared__ int64_t soff[kMaxZc + 1];            // entry-block offsets of the column's planes
     __shared__ R sA[4];
     __shared__ int abort_sh;
 
@@ -313,21 +318,6 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         abort_sh = 0;
         fence_proxy_async();
     }
-    if (tid < 3) sA[tid] = (R)Ak[tid];
-    if (tid == 3) sA[3] = (R)(0.5 * (Ak[0] * Ak[0] + Ak[1] * Ak[1] + Ak[2] * Ak[2]));
-    int cs = 0, na = 0;
-    if (NP > 0) {
-        if (tid <= nzc) soff[tid] = N.sblk_off[(int64_t)col * G.zc + tid];
-        cs = N.col_start[col];
-        na = N.col_start[col + 1] - cs;
-        for (int idx = tid; idx < na * NPV * VP; idx += NT) {
-            const int s = idx / (NPV * VP), r = idx - s * (NPV * VP), i = r / VP, jj = r - i * VP;
-            const int64_t a = N.col_atom[cs + s];
-            sP[idx] = __ldg(reinterpret_cast<const float4*>(N.Pin + (a * NPV + i) * 2 * G.ld + c0) + jj);
-        }
-    }
-    __syncthreads();
-
     auto issue = [&](int p) {   // TMA of plane p (z = z0 - 2 + p) into slot p % NSLOT
         const int s = p % NSLOT;
         const int zz = ((z0 - 2 + p) % G.nz + G.nz) % G.nz;
@@ -378,13 +368,31 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         for (int n = 0; n < 8; ++n) offN[n] = swz<VP>((int)(nb_ptr<VP>(ring, lx + dx[n], ly + dy[n], 0) - ring), vb);
     }
 
+    // the first planes and psi tiles are in flight while the column's
+    // projections are staged; the entry blocks need the staged offsets
     int issued = 0, waited = 0;                     // meaningful in thread 0
     if (tid == 0) {
         for (int p = 0; p < NSLOT && p < nplanes; ++p) issue(p);
         issued = min(NSLOT, nplanes);
-        for (int j = 0; j < ESL - 1; ++j) issue_e(j);
         for (int j = 0; j < PSL - 1; ++j) issue_psi(j);
     }
+    if (tid < 3) sA[tid] = (R)Ak[tid];
+    if (tid == 3) sA[3] = (R)(0.5 * (Ak[0] * Ak[0] + Ak[1] * Ak[1] + Ak[2] * Ak[2]));
+    int cs = 0, na = 0;
+    if (NP > 0) {
+        if (tid <= nzc) soff[tid] = N.sblk_off[(int64_t)col * G.zc + tid];
+        cs = N.col_start[col];
+        na = N.col_start[col + 1] - cs;
+        for (int idx = tid; idx < na * NPV * VP; idx += NT) {
+            const int s = idx / (NPV * VP), r = idx - s * (NPV * VP), i = r / VP, jj = r - i * VP;
+            const int64_t a = N.col_atom[cs + s];
+            sP[idx] = __ldg(reinterpret_cast<const float4*>(N.Pin + (a * NPV + i) * 2 * G.ld + c0) + jj);
+        }
+    }
+    __syncthreads();
+
+    if (tid == 0)
+        for (int j = 0; j < ESL - 1; ++j) issue_e(j);
     // register window of the thread's vectors: q[k][0..4] = planes z-2 .. z+2
     float4 q[NVT][5];
     bool ok = true;
@@ -988,6 +996,23 @@ TmaMaps maps_for(Domain& d, const void* base) {
 
 int chunks_of(const Domain& d) { return (int)((size_t)d.ld * d.elem / (d.tma->vp * 16)); }
 
+void set_zc(Domain& d, int zc) {
+    TmaState& t = *d.tma;
+    t.zc = zc;
+    t.ncols = (d.desc.n[0] / TX) * (d.desc.n[1] / TY) * ((d.desc.n[2] + zc - 1) / zc);
+}
+
+// Does the stage kernel with projectors keep five w slots at two CTAs per SM
+// in one of the chunk widths the tile tuner may pick?
+bool five_slots_fit(const Domain& d, int np, int maxs, int scap) {
+    if (!d.c64())
+        return (np == 4 ? smem_bytes<double, 8, 4>(maxs, 5, scap) : smem_bytes<double, 8, 8>(maxs, 5, scap)) <=
+               kTwoCtaSmem;
+    const size_t b4 = np == 4 ? smem_bytes<float, 4, 4>(maxs, 5, scap) : smem_bytes<float, 4, 8>(maxs, 5, scap);
+    const size_t b8 = np == 4 ? smem_bytes<float, 8, 4>(maxs, 5, scap) : smem_bytes<float, 8, 8>(maxs, 5, scap);
+    return b4 <= kTwoCtaSmem || (d.tma->vp == 8 && b8 <= kTwoCtaSmem);
+}
+
 }  // namespace
 
 void tma_setup(Domain& d) {
@@ -1001,12 +1026,13 @@ void tma_setup(Domain& d) {
     t.ok = t.vp != 0 && nx % TX == 0 && ny % TY == 0 && std::getenv("MLMD_NO_TMA") == nullptr;
     t.tuned = false;
     if (!t.ok) return;
-    // z range per CTA: enough CTAs to fill the GPU, at most 16 planes (fewer
-    // atoms per column keep the staged projections small)
+    // z range per CTA: enough CTAs to fill the GPU, at most kMaxZc planes
+    // (longer columns spread each CTA's start-up and its 4-plane z halo over
+    // more planes; the projector tables may cut this to 16, see tma_build_nl)
     const int base = (nx / TX) * (ny / TY) * chunks_of(d);
     const int nzch = std::max(1, std::min((608 + base - 1) / base, std::max(1, nz / 4)));
-    t.zc = std::min((nz + nzch - 1) / nzch, 16);
-    t.ncols = (nx / TX) * (ny / TY) * ((nz + t.zc - 1) / t.zc);
+    t.zc_full = std::min((nz + nzch - 1) / nzch, kMaxZc);
+    set_zc(d, t.zc_full);
 }
 
 void tma_release(Domain& d) {
@@ -1016,7 +1042,7 @@ void tma_release(Domain& d) {
 
 // Per-column tables of the fused nonlocal path, built on the host from the
 // device lists (set-up, not on the time-step path).
-void tma_build_nl(Domain& d, const double* D_host) {
+void tma_build_nl(Domain& d, const double* D_host, int zc_cap) {
     if (!d.tma || !d.tma->ok) return;
     TmaState& t = *d.tma;
     for (void* p : {(void*)t.col_start, (void*)t.col_atom, (void*)t.sblk, (void*)t.sblk_off, (void*)t.pp_seg,
@@ -1029,6 +1055,7 @@ void tma_build_nl(Domain& d, const double* D_host) {
     t.scap = 0;
     t.nl_ok = false;
     t.maxs = 0;
+    if (zc_cap == 0) set_zc(d, t.zc_full);
     const Nonlocal& nl = d.nl;
     if (nl.n_atoms == 0 || nl.n_list == 0) return;
     const int nx = d.desc.n[0], ny = d.desc.n[1];
@@ -1119,6 +1146,13 @@ void tma_build_nl(Domain& d, const double* D_host) {
                     t.scap = std::max<int>(t.scap, (int)(sblk.size() - sblk_off[blk]));
                 }
         sblk_off[(size_t)t.ncols * t.zc] = (int64_t)sblk.size();
+    }
+    // long columns gather more atoms: where their staged projections would
+    // cost the fifth w slot, build the tables again for 16-plane columns
+    if (t.zc > 16 && !five_slots_fit(d, np, t.maxs, t.scap)) {
+        set_zc(d, 16);
+        tma_build_nl(d, D_host, 16);
+        return;
     }
     // projection tables: projection columns of pzc planes, entries ordered by
     // (slot, plane, point); slots number a column's atoms in ascending order

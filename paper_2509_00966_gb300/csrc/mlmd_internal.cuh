@@ -230,7 +230,7 @@ void tma_release(Domain& d);
 int tma_blocks(const Domain& d);
 bool launch_stage_tma(Domain& d, const StageArgs& a, bool* proj_done);
 // Tables of the fused nonlocal path (after the projector lists are built).
-void tma_build_nl(Domain& d, const double* D_host);
+void tma_build_nl(Domain& d, const double* D_host, int zc_cap = 0);   // zc_cap: internal (16 on the rebuild)
 bool tma_fused_nl(const Domain& d);
 // Time both orbital-chunk widths of the TMA stage kernel once per domain and
 // keep the faster (no-op after the first call).  Must not run during stream
