@@ -287,10 +287,17 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     __shared__ int64_t soff[kMaxZc + 1];            // entry-block offsets of the column's planes
     __shared__ R sA[4];
     __shared__ int abort_sh;
+    __shared__ int iss[6];                          // thread 0's TMA issue state (see issue)
 
     const int tid = threadIdx.x;
-    const int pt = tid / TPP, jv = tid % TPP;       // point of the tile, first vector (then jv + TPP k)
-    const int lx = pt % TX, ly = pt / TX;
+    // point of the tile and first vector (then jv + TPP k); with 4 threads per
+    // point a warp holds a 4 x 2 block of points (its scatter loop runs as
+    // long as its busiest point, and compact blocks see more even sphere
+    // counts than a row of 8); two consecutive points are x neighbours, so
+    // the swizzled 16-byte loads stay free of bank conflicts
+    const int wp = tid / TPP, jv = tid % TPP;
+    const int lx = (wp & 3) + ((wp >> 3) & 1) * 4, ly = ((wp >> 2) & 1) + (wp >> 4) * 2;
+    const int pt = ly * TX + lx;                    // row-major index in the tile
     // grid (chunk, tile, z range): the chunks of one tile run side by side,
     // so each grid point's orbital row is read from DRAM in one stretch
     const int tile = blockIdx.y;
@@ -312,23 +319,36 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     const int col = tile + gridDim.y * blockIdx.z;
 
     if (tid == 0) {
+        iss[0] = (x0 - 2 + G.nx) % G.nx;
+        iss[1] = (x0 + TX) % G.nx;
+        iss[2] = (y0 - 2 + G.ny) % G.ny;
+        iss[3] = (y0 + TY) % G.ny;
+        iss[4] = ((z0 - 2) % G.nz + G.nz) % G.nz;
+        iss[5] = 0;
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
         for (int s = 0; s < ESL; ++s) mbar_init(&ebars[s], 1);
         for (int s = 0; s < PSL; ++s) mbar_init(&pbars[s], 1);
         abort_sh = 0;
         fence_proxy_async();
     }
-    auto issue = [&](int p) {   // TMA of plane p (z = z0 - 2 + p) into slot p % NSLOT
-        const int s = p % NSLOT;
-        const int zz = ((z0 - 2 + p) % G.nz + G.nz) % G.nz;
+    // TMA of the next plane, p = 0, 1, 2, ... in turn (z = z0 - 2 + p, slot
+    // p % NSLOT).  Only thread 0 issues, between the plane barriers that all
+    // warps wait at, so its share is kept to a few instructions: the wrapped
+    // halo origins and the running (z, slot) pair live in shared memory
+    // (iss[]: x-2, x+8, y-2, y+8, z, slot) instead of being recomputed with
+    // divisions by the grid size for every plane.
+    auto issue = [&]() {
+        const int s = iss[5], zz = iss[4];
         float4* d = ring + s * Slot<VP>::N;
         uint64_t* b = &bars[s];
         mbar_expect_tx(b, Slot<VP>::BYTES);
         tma_load_4d(d + Slot<VP>::C, &tm_c, c0, x0, y0, zz, b);
-        tma_load_4d(d + Slot<VP>::XM, &tm_x, c0, (x0 - 2 + G.nx) % G.nx, y0, zz, b);
-        tma_load_4d(d + Slot<VP>::XP, &tm_x, c0, (x0 + TX) % G.nx, y0, zz, b);
-        tma_load_4d(d + Slot<VP>::YM, &tm_y, c0, x0, (y0 - 2 + G.ny) % G.ny, zz, b);
-        tma_load_4d(d + Slot<VP>::YP, &tm_y, c0, x0, (y0 + TY) % G.ny, zz, b);
+        tma_load_4d(d + Slot<VP>::XM, &tm_x, c0, iss[0], y0, zz, b);
+        tma_load_4d(d + Slot<VP>::XP, &tm_x, c0, iss[1], y0, zz, b);
+        tma_load_4d(d + Slot<VP>::YM, &tm_y, c0, x0, iss[2], zz, b);
+        tma_load_4d(d + Slot<VP>::YP, &tm_y, c0, x0, iss[3], zz, b);
+        iss[4] = zz + 1 == G.nz ? 0 : zz + 1;
+        iss[5] = s + 1 == NSLOT ? 0 : s + 1;
     };
     auto wait_plane = [&](int p) -> bool { return mbar_wait_bounded(&bars[p % NSLOT], (uint32_t)((p / NSLOT) & 1)); };
     // scatter entry block of computed plane j (z = z0 + j) into entry slot j % ESL
@@ -372,7 +392,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     // projections are staged; the entry blocks need the staged offsets
     int issued = 0, waited = 0;                     // meaningful in thread 0
     if (tid == 0) {
-        for (int p = 0; p < NSLOT && p < nplanes; ++p) issue(p);
+        for (int p = 0; p < NSLOT && p < nplanes; ++p) issue();
         issued = min(NSLOT, nplanes);
         for (int j = 0; j < PSL - 1; ++j) issue_psi(j);
     }
@@ -411,7 +431,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     __syncthreads();
     if (tid == 0 && !aborted0 && issued < nplanes) {   // slot 0 (plane z0-2) is free again
         fence_proxy_async();
-        issue(issued);
+        issue();
         ++issued;
     }
 
@@ -446,7 +466,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             waited = i + 5;
             fence_proxy_async();
             if (issued < nplanes) {         // next plane into the slot of plane z-1
-                issue(issued);
+                issue();
                 ++issued;
             }
             issue_e(i + ESL - 1);           // into the entry slot of plane z-1
