@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     __shared__ int64_t soff[kMaxZc + 1];            // entry-block offsets of the column's planes
     __shared__ R sA[4];
     __shared__ int abort_sh;
-    __shared__ int iss[6];                          // thread 0's TMA issue state (see issue)
+    __shared__ int iss[9];                          // copy-issue state (see issue)
 
     const int tid = threadIdx.x;
     // point of the tile and first vector (then jv + TPP k); with 4 threads per
@@ -325,6 +325,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         iss[3] = (y0 + TY) % G.ny;
         iss[4] = ((z0 - 2) % G.nz + G.nz) % G.nz;
         iss[5] = 0;
+        iss[6] = iss[7] = iss[8] = 0;
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
         for (int s = 0; s < ESL; ++s) mbar_init(&ebars[s], 1);
         for (int s = 0; s < PSL; ++s) mbar_init(&pbars[s], 1);
@@ -332,11 +333,12 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         fence_proxy_async();
     }
     // TMA of the next plane, p = 0, 1, 2, ... in turn (z = z0 - 2 + p, slot
-    // p % NSLOT).  Only thread 0 issues, between the plane barriers that all
-    // warps wait at, so its share is kept to a few instructions: the wrapped
-    // halo origins and the running (z, slot) pair live in shared memory
-    // (iss[]: x-2, x+8, y-2, y+8, z, slot) instead of being recomputed with
-    // divisions by the grid size for every plane.
+    // p % NSLOT).  One thread issues right after each plane barrier (lane 0
+    // of warp i mod the warp count at plane i, so no warp carries the issue
+    // work every plane); the issue state lives in shared memory: the wrapped
+    // halo origins and the running (z, slot) pair, so no thread divides by
+    // the grid size per plane, and the copies issued so far on each ring
+    // (iss[]: x-2, x+8, y-2, y+8, z, slot, planes, entry blocks, psi tiles).
     auto issue = [&]() {
         const int s = iss[5], zz = iss[4];
         float4* d = ring + s * Slot<VP>::N;
@@ -349,10 +351,10 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         tma_load_4d(d + Slot<VP>::YP, &tm_y, c0, x0, iss[3], zz, b);
         iss[4] = zz + 1 == G.nz ? 0 : zz + 1;
         iss[5] = s + 1 == NSLOT ? 0 : s + 1;
+        iss[6] += 1;
     };
     auto wait_plane = [&](int p) -> bool { return mbar_wait_bounded(&bars[p % NSLOT], (uint32_t)((p / NSLOT) & 1)); };
     // scatter entry block of computed plane j (z = z0 + j) into entry slot j % ESL
-    int issued_e = 0, waited_e = 0;                 // meaningful in thread 0
     auto issue_e = [&](int j) {
         if (NP == 0 || j >= nzc) return;
         const int64_t eo = soff[j];
@@ -360,16 +362,15 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         uint64_t* b = &ebars[j % ESL];
         mbar_expect_tx(b, eb);
         bulk_g2s(sE + (size_t)(j % ESL) * N.scap, N.sblk + eo, eb, b);
-        issued_e = j + 1;
+        iss[7] = j + 1;
     };
     // psi tile of computed plane j (z = z0 + j) into psi slot j % PSL
-    int issued_p = 0, waited_p = 0;                 // meaningful in thread 0
     auto issue_psi = [&](int j) {
         if (psi_mode != 2 || j >= nzc) return;
         uint64_t* b = &pbars[j % PSL];
         mbar_expect_tx(b, Slot<VP>::PSI_BYTES);
         tma_load_4d(sPsi + (j % PSL) * Slot<VP>::PN, &tm_p, c0, x0, y0, z0 + j, b);
-        issued_p = j + 1;
+        iss[8] = j + 1;
     };
 
     // shared-memory offsets (16-byte vectors) of this thread's first vector and
@@ -390,10 +391,8 @@ __global__ void __launch_bounds__(64 * TPP, 2)
 
     // the first planes and psi tiles are in flight while the column's
     // projections are staged; the entry blocks need the staged offsets
-    int issued = 0, waited = 0;                     // meaningful in thread 0
     if (tid == 0) {
         for (int p = 0; p < NSLOT && p < nplanes; ++p) issue();
-        issued = min(NSLOT, nplanes);
         for (int j = 0; j < PSL - 1; ++j) issue_psi(j);
     }
     if (tid < 3) sA[tid] = (R)Ak[tid];
@@ -427,12 +426,10 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             for (int k = 0; k < NVT; ++k) q[k][p] = s[offC ^ k];
         }
     }
-    if (tid == 0) waited = aborted0 ? 0 : 4;
     __syncthreads();
-    if (tid == 0 && !aborted0 && issued < nplanes) {   // slot 0 (plane z0-2) is free again
+    if (tid == 0 && !aborted0 && iss[6] < nplanes) {   // slot 0 (plane z0-2) is free again
         fence_proxy_async();
         issue();
-        ++issued;
     }
 
     R acc[5] = {0, 0, 0, 0, 0};
@@ -462,13 +459,9 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         if (!ok) abort_sh = 1;
         __syncthreads();                    // also: all reads of the slot of plane z-1 are done
         if (abort_sh) break;
-        if (tid == 0) {
-            waited = i + 5;
+        if (tid == ((i & (NT / 32 - 1)) << 5)) {
             fence_proxy_async();
-            if (issued < nplanes) {         // next plane into the slot of plane z-1
-                issue();
-                ++issued;
-            }
+            if (iss[6] < nplanes) issue();  // next plane into the slot of plane z-1
             issue_e(i + ESL - 1);           // into the entry slot of plane z-1
             issue_psi(i + PSL - 1);         // into the psi slot of plane z-1
         }
@@ -600,7 +593,6 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         if (NP > 0) {
             e_ok = mbar_wait_bounded(&ebars[i % ESL], (uint32_t)((i / ESL) & 1));
             if (!e_ok) abort_sh = 1;
-            else if (tid == 0) waited_e = i + 1;
         }
         if (NP > 0 && e_ok) {   // scatter-back: sum_(a,i) b_ai(r) D_ai <b_ai|w>
             const unsigned char* eb = sE + (size_t)(i % ESL) * N.scap;
@@ -636,7 +628,6 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         }
         if (psi_mode == 2) {                // psi tile of this plane (issued two planes ago)
             if (!mbar_wait_bounded(&pbars[i % PSL], (uint32_t)((i / PSL) & 1))) abort_sh = 1;
-            if (tid == 0) waited_p = i + 1;
 #pragma unroll
             for (int k = 0; k < NVT; ++k) ps_cur[k] = sPsi[(i % PSL) * Slot<VP>::PN + (offPs ^ k)];
         }
@@ -704,14 +695,18 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             for (int w = 0; w < 4; ++w) q[k][w] = q[k][w + 1];
         }
     }
+    __syncthreads();                        // the issue counters and abort_sh are final
     if (abort_sh) {
         if (tid == 0) {
             atomicExch(err, 1);
-            // let the copies still in flight land before the CTA's shared memory goes away
-            for (int p = waited; p < issued; ++p) (void)wait_plane(p);
-            for (int j = waited_e; j < issued_e; ++j)
+            // let the copies still in flight land before the CTA's shared
+            // memory goes away: the latest copy issued into each slot of
+            // each ring (earlier ones into the same slot completed before it
+            // was issued; waiting on a completed phase returns at once)
+            for (int p = max(0, iss[6] - NSLOT); p < iss[6]; ++p) (void)wait_plane(p);
+            for (int j = max(0, iss[7] - ESL); j < iss[7]; ++j)
                 (void)mbar_wait_bounded(&ebars[j % ESL], (uint32_t)((j / ESL) & 1));
-            for (int j = waited_p; j < issued_p; ++j)
+            for (int j = max(0, iss[8] - PSL); j < iss[8]; ++j)
                 (void)mbar_wait_bounded(&pbars[j % PSL], (uint32_t)((j / PSL) & 1));
         }
     }
