@@ -448,14 +448,20 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     int64_t g = (x0 + lx) + (int64_t)G.nx * (y0 + ly) + plane_stride * z0;
     const int64_t row = 2 * (int64_t)G.ld;
     R vnext = nzc > 0 ? V[g] : (R)0;       // V one plane ahead
-    for (int i = 0; i < nzc && !aborted0; ++i, g += plane_stride) {
+    // running ring positions (no division per plane): slots of planes z and
+    // z+2 and the phase parity of the latter's barrier; the output row
+    int s2 = 2 % NSLOT, s4i = 4 % NSLOT;
+    uint32_t ph4 = (uint32_t)((4 / NSLOT) & 1);
+    R* orow = out + g * row + c0;
+    const int64_t orow_step = plane_stride * row;
+    for (int i = 0; i < nzc && !aborted0; ++i, g += plane_stride, orow += orow_step) {
         // per-point global loads first, so that they overlap the plane wait
         // and the shared-memory stencil
         const R vv = vnext;
         if (i + 1 < nzc) vnext = V[g + plane_stride];
         float4 ps_cur[NVT];
         // plane z+2 (p = i+4) must have landed
-        ok = wait_plane(i + 4);
+        ok = mbar_wait_bounded(&bars[s4i], ph4);
         if (!ok) abort_sh = 1;
         __syncthreads();                    // also: all reads of the slot of plane z-1 are done
         if (abort_sh) break;
@@ -465,8 +471,10 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             issue_e(i + ESL - 1);           // into the entry slot of plane z-1
             issue_psi(i + PSL - 1);         // into the psi slot of plane z-1
         }
-        const float4* sc = ring + ((i + 2) % NSLOT) * Slot<VP>::N;    // plane z
-        const float4* s4 = ring + ((i + 4) % NSLOT) * Slot<VP>::N;    // plane z+2
+        const float4* sc = ring + s2 * Slot<VP>::N;     // plane z
+        const float4* s4 = ring + s4i * Slot<VP>::N;    // plane z+2
+        s2 = s2 + 1 == NSLOT ? 0 : s2 + 1;
+        if (++s4i == NSLOT) { s4i = 0; ph4 ^= 1u; }
         Cv<R> hw[NVT], dd[NVT][OBS ? 3 : 1];
         float2 hp[NVT][2];                  // packed path: h w of the vector's two complex values
         float2 dlp[NVT][2][OBS ? 3 : 1];    // packed path with observables: gradient per axis
@@ -641,7 +649,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 const float2 gr2 = f2s((float)gre), gi2 = make_float2(-(float)gim, (float)gim);
                 const float2 o0 = f2fma(gi2, swp(hp[k][0]), f2fma(gr2, hp[k][0], lo2(ps)));
                 const float2 o1 = f2fma(gi2, swp(hp[k][1]), f2fma(gr2, hp[k][1], hi2(ps)));
-                *(reinterpret_cast<float4*>(out + g * row + c0) + vb + k) = make_float4(o0.x, o0.y, o1.x, o1.y);
+                *(reinterpret_cast<float4*>(orow) + vb + k) = make_float4(o0.x, o0.y, o1.x, o1.y);
                 if constexpr (OBS) {
                     // f |c|^2, f Re(c* h w) and f Re(c* (-i) dl_a), each as a packed
                     // pair whose halves add up to the term
@@ -677,7 +685,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 }
             }
             const float4 ov = pack(o);
-            *(reinterpret_cast<float4*>(out + g * row + c0) + vb + k) = ov;
+            *(reinterpret_cast<float4*>(orow) + vb + k) = ov;
             if constexpr (OBS) {
                 Cv<R> c;
                 unpack(q[k][2], c);
