@@ -56,12 +56,12 @@ STAGE_SRC = os.path.join(ROOT, "paper_2509_00966_gb300", "csrc", "k_stage_tma.cu
 # reports no traffic.  Per orbital*gridpoint, so that a capture on fewer
 # orbitals scales to the benchmark's orbital count.
 STAGE_TRAFFIC = {
-    # (312.9 + 184.8) + (547.2 + 194.5) + (547.1 + 194.1) + (545.1 + 184.9) MB over
+    # (314.2 + 184.5) + (547.1 + 194.7) + (547.1 + 194.2) + (544.5 + 184.7) MB over
     # the four launches, 48^3 x 256 orbitals
-    "c1": {"src_sha16": "ad6e83529a1142da", "bytes_per_unit": 677.6e6 / (48 ** 3 * 256)},
-    # (792.8 + 496.5) + (1332.0 + 506.7) + (1332.1 + 506.6) + (1330.1 + 498.1) MB over
+    "c1": {"src_sha16": "c38b5c5737da8bc7", "bytes_per_unit": 677.7e6 / (48 ** 3 * 256)},
+    # (791.4 + 496.4) + (1332.8 + 506.2) + (1332.6 + 506.7) + (1330.0 + 498.2) MB over
     # the four launches, the c2 grid and projectors on 256 of its 1024 orbitals
-    "c2": {"src_sha16": "ad6e83529a1142da", "bytes_per_unit": 1698.7e6 / (64 ** 3 * 256)},
+    "c2": {"src_sha16": "c38b5c5737da8bc7", "bytes_per_unit": 1698.5e6 / (64 ** 3 * 256)},
 }
 
 
