@@ -125,6 +125,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait on one phase of an mbarrier: false after ~kWaitCycles.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;     // the usual case: no clock read
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
         if (clock64() - t0 > kWaitCycles) return false;
@@ -162,13 +163,12 @@ template <int VP> struct Slot {
     static constexpr int PN = TY * TX * VP;       // vectors of a psi tile
     static constexpr uint32_t PSI_BYTES = PN * 16;
 };
-// Scatter entry blocks have a ring of their own: the block of computed plane
-// j is brought two planes ahead of its use into slot j % ESL.
-constexpr int ESL = 2;
-// psi's centre tiles (when they come by TMA) have a ring of PSL slots.  One
-// plane of look-ahead for both is enough; the shared memory goes to a fifth
-// w slot instead (two planes of w in flight).
-constexpr int PSL = 2;
+// The scatter entry block and (when it comes by TMA) psi's centre tile of
+// computed plane j share a ring of XSL slots and one mbarrier per slot; they
+// are brought one plane ahead of their use into slot j % XSL.  One plane of
+// look-ahead is enough; the shared memory goes to a fifth w slot instead
+// (two planes of w in flight).
+constexpr int XSL = 2;
 
 // Vector (x+dx, y+dy) of the plane in slot s, one of dx, dy zero, |d| <= 2.
 template <int VP>
@@ -278,16 +278,15 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     // TMA destinations on a 1024-byte boundary (the launch adds 1024 bytes of
     // slack): the swizzle pattern is a function of the address bits
     float4* ring = reinterpret_cast<float4*>(smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u));
-    float4* sPsi = ring + NSLOT * Slot<VP>::N;      // [PSL][TY][TX][VP] psi tiles
-    float4* sP = sPsi + PSL * Slot<VP>::PN;         // [maxs][NP][VP] staged <b|w>
-    unsigned char* sE = reinterpret_cast<unsigned char*>(sP + N.maxs * NPV * VP);   // [ESL][scap] entry blocks
+    float4* sPsi = ring + NSLOT * Slot<VP>::N;      // [XSL][TY][TX][VP] psi tiles
+    float4* sP = sPsi + XSL * Slot<VP>::PN;         // [maxs][NP][VP] staged <b|w>
+    unsigned char* sE = reinterpret_cast<unsigned char*>(sP + N.maxs * NPV * VP);   // [XSL][scap] entry blocks
     __shared__ __align__(8) uint64_t bars[NSLOT];
-    __shared__ __align__(8) uint64_t ebars[ESL];
-    __shared__ __align__(8) uint64_t pbars[PSL];
+    __shared__ __align__(8) uint64_t xbars[XSL];
     __shared__ int64_t soff[kMaxZc + 1];            // entry-block offsets of the column's planes
     __shared__ R sA[4];
     __shared__ int abort_sh;
-    __shared__ int iss[9];                          // copy-issue state (see issue)
+    __shared__ int iss[8];                          // copy-issue state (see issue)
 
     const int tid = threadIdx.x;
     // point of the tile and first vector (then jv + TPP k); with 4 threads per
@@ -325,10 +324,9 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         iss[3] = (y0 + TY) % G.ny;
         iss[4] = ((z0 - 2) % G.nz + G.nz) % G.nz;
         iss[5] = 0;
-        iss[6] = iss[7] = iss[8] = 0;
+        iss[6] = iss[7] = 0;
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
-        for (int s = 0; s < ESL; ++s) mbar_init(&ebars[s], 1);
-        for (int s = 0; s < PSL; ++s) mbar_init(&pbars[s], 1);
+        for (int s = 0; s < XSL; ++s) mbar_init(&xbars[s], 1);
         abort_sh = 0;
         fence_proxy_async();
     }
@@ -338,7 +336,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     // work every plane); the issue state lives in shared memory: the wrapped
     // halo origins and the running (z, slot) pair, so no thread divides by
     // the grid size per plane, and the copies issued so far on each ring
-    // (iss[]: x-2, x+8, y-2, y+8, z, slot, planes, entry blocks, psi tiles).
+    // (iss[]: x-2, x+8, y-2, y+8, z, slot, planes, entry / psi pairs).
     auto issue = [&]() {
         const int s = iss[5], zz = iss[4];
         float4* d = ring + s * Slot<VP>::N;
@@ -354,23 +352,22 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         iss[6] += 1;
     };
     auto wait_plane = [&](int p) -> bool { return mbar_wait_bounded(&bars[p % NSLOT], (uint32_t)((p / NSLOT) & 1)); };
-    // scatter entry block of computed plane j (z = z0 + j) into entry slot j % ESL
-    auto issue_e = [&](int j) {
-        if (NP == 0 || j >= nzc) return;
-        const int64_t eo = soff[j];
-        const uint32_t eb = (uint32_t)(soff[j + 1] - eo);     // >= the 272-byte header
-        uint64_t* b = &ebars[j % ESL];
-        mbar_expect_tx(b, eb);
-        bulk_g2s(sE + (size_t)(j % ESL) * N.scap, N.sblk + eo, eb, b);
+    // entry block and psi tile of computed plane j (z = z0 + j) into slot
+    // j % XSL, both on that slot's barrier (nothing when neither is used)
+    const bool has_x = NP > 0 || psi_mode == 2;
+    auto issue_x = [&](int j) {
+        if (!has_x || j >= nzc) return;
+        uint64_t* b = &xbars[j % XSL];
+        int64_t eo = 0;
+        uint32_t eb = 0;
+        if (NP > 0) {
+            eo = soff[j];
+            eb = (uint32_t)(soff[j + 1] - eo);      // >= the 272-byte header
+        }
+        mbar_expect_tx(b, eb + (psi_mode == 2 ? Slot<VP>::PSI_BYTES : 0u));
+        if (NP > 0) bulk_g2s(sE + (size_t)(j % XSL) * N.scap, N.sblk + eo, eb, b);
+        if (psi_mode == 2) tma_load_4d(sPsi + (j % XSL) * Slot<VP>::PN, &tm_p, c0, x0, y0, z0 + j, b);
         iss[7] = j + 1;
-    };
-    // psi tile of computed plane j (z = z0 + j) into psi slot j % PSL
-    auto issue_psi = [&](int j) {
-        if (psi_mode != 2 || j >= nzc) return;
-        uint64_t* b = &pbars[j % PSL];
-        mbar_expect_tx(b, Slot<VP>::PSI_BYTES);
-        tma_load_4d(sPsi + (j % PSL) * Slot<VP>::PN, &tm_p, c0, x0, y0, z0 + j, b);
-        iss[8] = j + 1;
     };
 
     // shared-memory offsets (16-byte vectors) of this thread's first vector and
@@ -393,7 +390,6 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     // projections are staged; the entry blocks need the staged offsets
     if (tid == 0) {
         for (int p = 0; p < NSLOT && p < nplanes; ++p) issue();
-        for (int j = 0; j < PSL - 1; ++j) issue_psi(j);
     }
     if (tid < 3) sA[tid] = (R)Ak[tid];
     if (tid == 3) sA[3] = (R)(0.5 * (Ak[0] * Ak[0] + Ak[1] * Ak[1] + Ak[2] * Ak[2]));
@@ -411,7 +407,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
     __syncthreads();
 
     if (tid == 0)
-        for (int j = 0; j < ESL - 1; ++j) issue_e(j);
+        for (int j = 0; j < XSL - 1; ++j) issue_x(j);
     // register window of the thread's vectors: q[k][0..4] = planes z-2 .. z+2
     float4 q[NVT][5];
     bool ok = true;
@@ -468,8 +464,7 @@ __global__ void __launch_bounds__(64 * TPP, 2)
         if (tid == ((i & (NT / 32 - 1)) << 5)) {
             fence_proxy_async();
             if (iss[6] < nplanes) issue();  // next plane into the slot of plane z-1
-            issue_e(i + ESL - 1);           // into the entry slot of plane z-1
-            issue_psi(i + PSL - 1);         // into the psi slot of plane z-1
+            issue_x(i + XSL - 1);           // into the entry / psi slot of plane z-1
         }
         const float4* sc = ring + s2 * Slot<VP>::N;     // plane z
         const float4* s4 = ring + s4i * Slot<VP>::N;    // plane z+2
@@ -595,15 +590,16 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             }
         }
         }
-        // the entry block of this plane must have landed; on a timeout the
-        // scatter is skipped (the CTA aborts) rather than read a stale block
+        // the entry block and psi tile of this plane must have landed; on a
+        // timeout the scatter is skipped (the CTA aborts) rather than read a
+        // stale block
         bool e_ok = true;
-        if (NP > 0) {
-            e_ok = mbar_wait_bounded(&ebars[i % ESL], (uint32_t)((i / ESL) & 1));
+        if (has_x) {
+            e_ok = mbar_wait_bounded(&xbars[i % XSL], (uint32_t)((i / XSL) & 1));
             if (!e_ok) abort_sh = 1;
         }
         if (NP > 0 && e_ok) {   // scatter-back: sum_(a,i) b_ai(r) D_ai <b_ai|w>
-            const unsigned char* eb = sE + (size_t)(i % ESL) * N.scap;
+            const unsigned char* eb = sE + (size_t)(i % XSL) * N.scap;
             const int32_t* hdr = reinterpret_cast<const int32_t*>(eb);
             const int32_t* eslot = hdr + 68;
             const R* ebd = reinterpret_cast<const R*>(eb + 272 + 4 * hdr[66]);
@@ -634,10 +630,9 @@ __global__ void __launch_bounds__(64 * TPP, 2)
                 }
             }
         }
-        if (psi_mode == 2) {                // psi tile of this plane (issued two planes ago)
-            if (!mbar_wait_bounded(&pbars[i % PSL], (uint32_t)((i / PSL) & 1))) abort_sh = 1;
+        if (psi_mode == 2) {                // psi tile of this plane (landed with the entry block)
 #pragma unroll
-            for (int k = 0; k < NVT; ++k) ps_cur[k] = sPsi[(i % PSL) * Slot<VP>::PN + (offPs ^ k)];
+            for (int k = 0; k < NVT; ++k) ps_cur[k] = sPsi[(i % XSL) * Slot<VP>::PN + (offPs ^ k)];
         }
 #pragma unroll
         for (int k = 0; k < NVT; ++k) {
@@ -712,10 +707,8 @@ __global__ void __launch_bounds__(64 * TPP, 2)
             // each ring (earlier ones into the same slot completed before it
             // was issued; waiting on a completed phase returns at once)
             for (int p = max(0, iss[6] - NSLOT); p < iss[6]; ++p) (void)wait_plane(p);
-            for (int j = max(0, iss[7] - ESL); j < iss[7]; ++j)
-                (void)mbar_wait_bounded(&ebars[j % ESL], (uint32_t)((j / ESL) & 1));
-            for (int j = max(0, iss[8] - PSL); j < iss[8]; ++j)
-                (void)mbar_wait_bounded(&pbars[j % PSL], (uint32_t)((j / PSL) & 1));
+            for (int j = max(0, iss[7] - XSL); j < iss[7]; ++j)
+                (void)mbar_wait_bounded(&xbars[j % XSL], (uint32_t)((j / XSL) & 1));
         }
     }
     if constexpr (OBS) {
@@ -890,8 +883,8 @@ constexpr size_t kTwoCtaSmem = 113 * 1024;
 template <typename R, int VP, int NP>
 size_t smem_bytes(int maxs, int nslot, int scap) {
     const int npv = NP > 0 ? NP : 1;
-    size_t b = (size_t)nslot * Slot<VP>::N * 16 + (size_t)PSL * Slot<VP>::PSI_BYTES;
-    if (NP > 0) b += (size_t)maxs * npv * VP * 16 + (size_t)ESL * scap;
+    size_t b = (size_t)nslot * Slot<VP>::N * 16 + (size_t)XSL * Slot<VP>::PSI_BYTES;
+    if (NP > 0) b += (size_t)maxs * npv * VP * 16 + (size_t)XSL * scap;
     return b + 1024;
 }
 
