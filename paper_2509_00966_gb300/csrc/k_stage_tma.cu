@@ -740,9 +740,9 @@ __global__ void __launch_bounds__(64 * TPP, 2)
 
 // <b|W> for every atom, by projection columns (an 8 x 8 tile of points, one
 // orbital chunk, PZC planes).  Thread 0 brings the column's W planes (one
-// TMA each) and its entries -- W row (plane * 64 + point) and beta, ordered
-// by (slot, plane, point) -- (two bulk copies) into shared memory, all on
-// one mbarrier.  The entries are cut into eight equal runs, one per warp;
+// TMA each, issued before the column's index loads) and its entries -- W
+// row (plane * 64 + point) and beta, ordered by (slot, plane, point) -- (two
+// bulk copies) into shared memory, all on one mbarrier.  The entries are cut into eight equal runs, one per warp;
 // a warp walks the atoms (slots) its run overlaps and, for each, the
 // entries in both, with the lanes split over (entry group, projector,
 // 16-byte vector), then adds the atom's sum to Pout with one vector atomic.
@@ -770,21 +770,29 @@ __global__ void __launch_bounds__(256) k_nl_project_cols(const __grid_constant__
     const int z0 = blockIdx.z * pzc;
     const int nzc = min(pzc, nz - z0);
     const int c0 = blockIdx.x * OCR;
+    // the W planes go out first (they need no index), two arrivals on the
+    // barrier: the planes' and, once the column's ranges are known, the
+    // entries'
+    if (tid == 0) {
+        mbar_init(&bar, 2);
+        abort_sh = 0;
+        fence_proxy_async();
+        mbar_expect_tx(&bar, (uint32_t)nzc * 64 * VP * 16);
+        for (int iz = 0; iz < nzc; ++iz) tma_load_4d(base + (size_t)iz * 64 * VP * 16, &tm_c, c0, x0, y0, z0 + iz, &bar);
+    }
     const int k0 = N.pp_atom_start[pcol], k1 = N.pp_atom_start[pcol + 1];   // the column's slots
     const int e0 = N.pp_seg[k0], e1 = N.pp_seg[k1];
-    if (e1 == e0) return;
     const int a0 = e0 & ~3, a1 = (e1 + 3) & ~3;
     const int32_t* sRow = reinterpret_cast<const int32_t*>(base + wbytes) - a0;
     const R* sB = reinterpret_cast<const R*>(base + wbytes + kbytes) - (int64_t)e0 * NP;
     if (tid == 0) {
-        mbar_init(&bar, 1);
-        abort_sh = 0;
-        fence_proxy_async();
-        mbar_expect_tx(&bar, (uint32_t)(a1 - a0) * 4 + (uint32_t)(e1 - e0) * NP * sizeof(R) +
-                                 (uint32_t)nzc * 64 * VP * 16);
-        bulk_g2s(base + wbytes, N.pp_key + a0, (uint32_t)(a1 - a0) * 4, &bar);
-        bulk_g2s(base + wbytes + kbytes, N.pp_beta + (int64_t)e0 * NP, (uint32_t)(e1 - e0) * NP * sizeof(R), &bar);
-        for (int iz = 0; iz < nzc; ++iz) tma_load_4d(base + (size_t)iz * 64 * VP * 16, &tm_c, c0, x0, y0, z0 + iz, &bar);
+        // (an empty column expects no entry bytes: its barrier completes with the planes)
+        mbar_expect_tx(&bar, e1 > e0 ? (uint32_t)(a1 - a0) * 4 + (uint32_t)(e1 - e0) * NP * sizeof(R) : 0u);
+        if (e1 > e0) {
+            bulk_g2s(base + wbytes, N.pp_key + a0, (uint32_t)(a1 - a0) * 4, &bar);
+            bulk_g2s(base + wbytes + kbytes, N.pp_beta + (int64_t)e0 * NP, (uint32_t)(e1 - e0) * NP * sizeof(R),
+                     &bar);
+        }
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(&bar, 0);
