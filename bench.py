@@ -56,12 +56,12 @@ STAGE_SRC = os.path.join(ROOT, "paper_2509_00966_gb300", "csrc", "k_stage_tma.cu
 # reports no traffic.  Per orbital*gridpoint, so that a capture on fewer
 # orbitals scales to the benchmark's orbital count.
 STAGE_TRAFFIC = {
-    # (314.2 + 184.5) + (547.1 + 194.7) + (547.1 + 194.2) + (544.5 + 184.7) MB over
+    # (313.4 + 184.5) + (547.1 + 194.5) + (547.1 + 194.5) + (544.4 + 184.8) MB over
     # the four launches, 48^3 x 256 orbitals
-    "c1": {"src_sha16": "c38b5c5737da8bc7", "bytes_per_unit": 677.7e6 / (48 ** 3 * 256)},
-    # (791.4 + 496.4) + (1332.8 + 506.2) + (1332.6 + 506.7) + (1330.0 + 498.2) MB over
+    "c1": {"src_sha16": "d48f7dca71e0a6fa", "bytes_per_unit": 677.6e6 / (48 ** 3 * 256)},
+    # (793.2 + 496.7) + (1333.1 + 506.4) + (1333.4 + 507.0) + (1329.9 + 497.8) MB over
     # the four launches, the c2 grid and projectors on 256 of its 1024 orbitals
-    "c2": {"src_sha16": "c38b5c5737da8bc7", "bytes_per_unit": 1698.5e6 / (64 ** 3 * 256)},
+    "c2": {"src_sha16": "d48f7dca71e0a6fa", "bytes_per_unit": 1699.4e6 / (64 ** 3 * 256)},
 }
 
 
