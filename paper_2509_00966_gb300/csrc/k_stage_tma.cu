@@ -1056,6 +1056,12 @@ void tma_setup(Domain& d) {
     const int base = (nx / TX) * (ny / TY) * chunks_of(d);
     const int nzch = std::max(1, std::min((608 + base - 1) / base, std::max(1, nz / 4)));
     t.zc_full = std::min((nz + nzch - 1) / nzch, kMaxZc);
+    // MLMD_STAGE_ZC (1..32) fixes the planes per column instead (tests and
+    // profiles; the projector tables may still cut it to 16)
+    if (const char* e = std::getenv("MLMD_STAGE_ZC")) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= kMaxZc) t.zc_full = std::min(v, nz);
+    }
     set_zc(d, t.zc_full);
 }
 

@@ -413,3 +413,24 @@ def test_invalid_calls_return_status():
         d.excitation()     # no reference orbitals yet
     assert e.value.status == 6
     d.close()
+
+
+@pytest.mark.parametrize("zc,precision,n_proj,n_atoms,r_cut", [
+    (3, "c64", 4, 7, 2.6),       # many short columns, the last one ragged (20 = 6 x 3 + 2)
+    (7, "c64", 8, 7, 2.6),       # odd column length, ragged last column
+    (20, "c64", 8, 7, 2.6),      # one column over the whole z extent (above 16 planes)
+    (32, "c128", 4, 7, 2.6),     # longer than the grid: clamped to it
+    (20, "c64", 8, 40, 3.0),     # dense projectors: the tables may fall back to 16-plane columns
+])
+def test_stage_column_lengths(zc, precision, n_proj, n_atoms, r_cut, monkeypatch):
+    """The z extent of the TMA stage kernel's columns (planes per CTA, up to
+    32 where the staged projections leave room for five w slots), fixed
+    through MLMD_STAGE_ZC, against the oracle: the plane ring, the entry and
+    psi copies and the halo planes wrap the same way at any column length."""
+    monkeypatch.setenv("MLMD_STAGE_ZC", str(zc))
+    spec = small_spec(precision=precision, n=(16, 16, 20), n_orb=48, steps=6, n_atoms=n_atoms, n_proj=n_proj,
+                      r_cut=r_cut)
+    tol = 1e-12 if precision == "c128" else 1e-5
+    out, obs, ref, robs = _run_both(spec)
+    assert np.max(np.abs(out - ref)) <= tol
+    _check_obs(obs, robs, 1e-11 if precision == "c128" else 1e-6)
