@@ -295,17 +295,20 @@ __global__ void __launch_bounds__(256) k_chol_rows(double* __restrict__ S, int n
 }
 
 // Trailing update after block column kb: S[i][k] -= sum_j L[i][j] conj(L[k][j])
-// for i >= k >= (kb+1)*32 (lower triangle), j over the panel.  32 x 32 output
-// tiles, 256 threads, 4 outputs each.
+// for i >= k >= (kb+1)*32 (lower triangle), j over the panel.  16 x 16 output
+// tiles, one output per thread: the late panels' small trailing matrices
+// still spread over many SMs (a 32 x 32 tile took ~55 us however few tiles
+// a panel had).
+constexpr int TT = 16;
 __global__ void __launch_bounds__(256) k_chol_trail(double* __restrict__ S, int n, int kb) {
     const int c0 = kb * CB, nb = min(CB, n - c0);
     const int base = c0 + nb;
     const int ti = blockIdx.y, tk = blockIdx.x;
     if (tk > ti) return;
-    const int i0 = base + ti * CB, k0 = base + tk * CB;
+    const int i0 = base + ti * TT, k0 = base + tk * TT;
     if (i0 >= n || k0 >= n) return;
-    __shared__ double Li[CB][CB + 1][2], Lk[CB][CB + 1][2];
-    for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
+    __shared__ double Li[TT][CB + 1][2], Lk[TT][CB + 1][2];
+    for (int e = threadIdx.x; e < TT * CB; e += blockDim.x) {
         const int r = e / CB, j = e % CB;
         const bool ini = i0 + r < n && j < nb, ink = k0 + r < n && j < nb;
         Li[r][j][0] = ini ? S[((int64_t)(i0 + r) * n + c0 + j) * 2] : 0.0;
@@ -314,19 +317,17 @@ __global__ void __launch_bounds__(256) k_chol_trail(double* __restrict__ S, int 
         Lk[r][j][1] = ink ? S[((int64_t)(k0 + r) * n + c0 + j) * 2 + 1] : 0.0;
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < CB * CB; o += blockDim.x) {
-        const int r = o / CB, c = o % CB;
-        const int i = i0 + r, k = k0 + c;
-        if (i >= n || k >= n || k > i) continue;
-        double sr = 0.0, si = 0.0;
-        for (int j = 0; j < nb; ++j) {
-            const double ar = Li[r][j][0], ai = Li[r][j][1], br = Lk[c][j][0], bi = -Lk[c][j][1];
-            sr += ar * br - ai * bi;
-            si += ar * bi + ai * br;
-        }
-        S[((int64_t)i * n + k) * 2] -= sr;
-        S[((int64_t)i * n + k) * 2 + 1] -= si;
+    const int r = threadIdx.x / TT, c = threadIdx.x % TT;
+    const int i = i0 + r, k = k0 + c;
+    if (i >= n || k >= n || k > i) return;
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        const double ar = Li[r][j][0], ai = Li[r][j][1], br = Lk[c][j][0], bi = -Lk[c][j][1];
+        sr += ar * br - ai * bi;
+        si += ar * bi + ai * br;
     }
+    S[((int64_t)i * n + k) * 2] -= sr;
+    S[((int64_t)i * n + k) * 2 + 1] -= si;
 }
 
 // X = L^{-1} (lower), recursively by blocks.  First every 32 x 32 diagonal
@@ -410,19 +411,25 @@ __device__ __forceinline__ void tile_mac(Tile32& t, const double* A, int lda, in
     __syncthreads();
 }
 
-// T_p = L_CA X_AA for every pair p of level b (T_p: [nc][b], leading dim b).
-// X_AA is lower triangular: only k >= the output column tile contributes.
-// Grid (b/32, b/32, pairs).
+// T_p = L_CA X_AA for every pair p of level b (T_p: [nc][b], leading dim b,
+// zeroed by the caller).  X_AA is lower triangular: only k >= the output
+// column tile contributes.  Split over K: each CTA adds one 32-wide K-tile's
+// product to its output tile with FP64 atomics, so that a level's work
+// spreads over as many CTAs as it has (tile, K-tile) pairs instead of
+// running each tile's K-tiles one after another (~55 us each).  Grid (b/32,
+// b/32, pairs * b/32): z = pair * (b/32) + K-tile.
 __global__ void __launch_bounds__(256) k_trinv_t(const double* __restrict__ L, const double* __restrict__ X, int n,
                                                  int b, double* __restrict__ T) {
     __shared__ Tile32 t;
-    const int p = blockIdx.z, a0 = 2 * p * b, cc0 = a0 + b;
+    const int nkt = b / CB;
+    const int p = blockIdx.z / nkt, kt = blockIdx.z % nkt;
+    const int a0 = 2 * p * b, cc0 = a0 + b;
     const int nc = min(b, n - cc0);
     const int ti = blockIdx.y * CB, tj = blockIdx.x * CB;
-    if (ti >= nc) return;
+    const int k0 = kt * CB;
+    if (ti >= nc || k0 < tj) return;
     double acc[2][2][2] = {};
-    for (int k0 = tj; k0 < b; k0 += CB)
-        tile_mac(t, L, n, cc0 + ti, a0 + k0, min(CB, nc - ti), CB, X, n, a0 + k0, a0 + tj, CB, CB, acc);
+    tile_mac(t, L, n, cc0 + ti, a0 + k0, min(CB, nc - ti), CB, X, n, a0 + k0, a0 + tj, CB, CB, acc);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double* Tp = T + (int64_t)p * b * b * 2;
 #pragma unroll
@@ -431,26 +438,30 @@ __global__ void __launch_bounds__(256) k_trinv_t(const double* __restrict__ L, c
         for (int q = 0; q < 2; ++q) {
             const int r = ti + ty + 16 * pp, c = tj + tx + 16 * q;
             if (r < nc) {
-                Tp[((int64_t)r * b + c) * 2] = acc[pp][q][0];
-                Tp[((int64_t)r * b + c) * 2 + 1] = acc[pp][q][1];
+                atomicAdd(&Tp[((int64_t)r * b + c) * 2], acc[pp][q][0]);
+                atomicAdd(&Tp[((int64_t)r * b + c) * 2 + 1], acc[pp][q][1]);
             }
         }
 }
 
 // X_CA = -X_CC T_p; X_CC is lower triangular: only k < the end of the output
-// row tile contributes.  Grid (b/32, b/32, pairs).
+// row tile contributes.  X_CA is zero before (X starts zeroed and each block
+// is written at one level only); split over K like k_trinv_t.  Grid (b/32,
+// b/32, pairs * b/32).
 __global__ void __launch_bounds__(256) k_trinv_x(const double* __restrict__ T, double* __restrict__ X, int n, int b) {
     __shared__ Tile32 t;
-    const int p = blockIdx.z, a0 = 2 * p * b, cc0 = a0 + b;
+    const int nkt = b / CB;
+    const int p = blockIdx.z / nkt, kt = blockIdx.z % nkt;
+    const int a0 = 2 * p * b, cc0 = a0 + b;
     const int nc = min(b, n - cc0);
     const int ti = blockIdx.y * CB, tj = blockIdx.x * CB;
-    if (ti >= nc) return;
+    const int k0 = kt * CB;
+    const int kend = min(nc, ti + CB);
+    if (ti >= nc || k0 >= kend) return;
     const double* Tp = T + (int64_t)p * b * b * 2;
     double acc[2][2][2] = {};
-    const int kend = min(nc, ti + CB);
-    for (int k0 = 0; k0 < kend; k0 += CB)
-        tile_mac(t, X, n, cc0 + ti, cc0 + k0, min(CB, nc - ti), min(CB, nc - k0), Tp, b, k0, tj, min(CB, nc - k0), CB,
-                 acc);
+    tile_mac(t, X, n, cc0 + ti, cc0 + k0, min(CB, nc - ti), min(CB, nc - k0), Tp, b, k0, tj, min(CB, nc - k0), CB,
+             acc);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int pp = 0; pp < 2; ++pp)
@@ -458,8 +469,8 @@ __global__ void __launch_bounds__(256) k_trinv_x(const double* __restrict__ T, d
         for (int q = 0; q < 2; ++q) {
             const int r = ti + ty + 16 * pp, c = tj + tx + 16 * q;
             if (r < nc) {
-                X[((int64_t)(cc0 + r) * n + a0 + c) * 2] = -acc[pp][q][0];
-                X[((int64_t)(cc0 + r) * n + a0 + c) * 2 + 1] = -acc[pp][q][1];
+                atomicAdd(&X[((int64_t)(cc0 + r) * n + a0 + c) * 2], -acc[pp][q][0]);
+                atomicAdd(&X[((int64_t)(cc0 + r) * n + a0 + c) * 2 + 1], -acc[pp][q][1]);
             }
         }
 }
@@ -591,7 +602,7 @@ void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info) {
             d.launches++;
         }
         if (below > 0) {
-            const int t = (below + CB - 1) / CB;
+            const int t = (below + TT - 1) / TT;
             k_chol_trail<<<dim3(t, t), 256, 0, d.stream>>>(S, n, kb);
             d.launches++;
         }
@@ -604,7 +615,8 @@ void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info) {
     d.launches++;
     for (int b = CB; b < n; b *= 2) {
         const int pairs = (n - b + 2 * b - 1) / (2 * b);      // pairs whose C block is non-empty
-        const dim3 grid(b / CB, b / CB, pairs);
+        const dim3 grid(b / CB, b / CB, pairs * (b / CB));    // (tile column, tile row, pair x K-tile)
+        MLMD_CUDA(cudaMemsetAsync(T, 0, (size_t)pairs * b * b * 2 * sizeof(double), d.stream));
         k_trinv_t<<<grid, 256, 0, d.stream>>>(S, X, n, b, T);
         k_trinv_x<<<grid, 256, 0, d.stream>>>(T, X, n, b);
         d.launches += 2;
