@@ -507,6 +507,12 @@ mlmd_status mlmd_domain_destroy(mlmd_domain_t dom) {
     dom->prof.destroy();
     tma_release(*dom);
     nl_tc_release(*dom);
+    if (dom->side) {
+        if (cudaStreamSynchronize(dom->side) != cudaSuccess) e = cudaErrorUnknown;
+        (void)cudaStreamDestroy(dom->side);
+    }
+    if (dom->ev_rows) (void)cudaEventDestroy(dom->ev_rows);
+    if (dom->ev_trail) (void)cudaEventDestroy(dom->ev_trail);
     delete dom;
     return e == cudaSuccess ? MLMD_OK : MLMD_ERR_CUDA;
 }

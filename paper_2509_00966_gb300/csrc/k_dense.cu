@@ -300,10 +300,12 @@ __global__ void __launch_bounds__(256) k_chol_rows(double* __restrict__ S, int n
 // still spread over many SMs (a 32 x 32 tile took ~55 us however few tiles
 // a panel had).
 constexpr int TT = 16;
-__global__ void __launch_bounds__(256) k_chol_trail(double* __restrict__ S, int n, int kb) {
+// (tk0, ti0): first tile column and row of the launch, so that the next
+// block column (tile columns 0 and 1) and the rest can go separately.
+__global__ void __launch_bounds__(256) k_chol_trail(double* __restrict__ S, int n, int kb, int tk0, int ti0) {
     const int c0 = kb * CB, nb = min(CB, n - c0);
     const int base = c0 + nb;
-    const int ti = blockIdx.y, tk = blockIdx.x;
+    const int ti = ti0 + blockIdx.y, tk = tk0 + blockIdx.x;
     if (tk > ti) return;
     const int i0 = base + ti * TT, k0 = base + tk * TT;
     if (i0 >= n || k0 >= n) return;
@@ -593,20 +595,45 @@ void cholesky_inverse_upper(Domain& d, double* S, double* Minv, int* d_info) {
     MLMD_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), d.stream));
     const int nblk = (n + CB - 1) / CB;
     double* Ld = (double*)d.mem.get((size_t)nblk * CB * CB * 2 * sizeof(double));
+    // Look-ahead: the trailing update of panel kb is split into the next
+    // block column (tile columns 0 and 1, main stream: the next diagonal
+    // block and panel rows need it) and the rest (side stream), so that the
+    // next panel's serial factorisation runs beside the bulk of the update.
+    // Ordering: the side update of panel kb starts after panel kb's rows;
+    // the main stream waits for it before panel kb+1's trailing update (both
+    // touch block column kb+2), which precedes every later diagonal block.
+    if (!d.side) {
+        MLMD_CUDA(cudaStreamCreateWithFlags(&d.side, cudaStreamNonBlocking));
+        MLMD_CUDA(cudaEventCreateWithFlags(&d.ev_rows, cudaEventDisableTiming));
+        MLMD_CUDA(cudaEventCreateWithFlags(&d.ev_trail, cudaEventDisableTiming));
+    }
+    bool side_pending = false;
     for (int kb = 0; kb < nblk; ++kb) {
         const int below = n - (kb * CB + std::min(CB, n - kb * CB));
         k_chol_diag<<<1, 256, 0, d.stream>>>(S, n, kb, Ld, d_info);
         d.launches++;
-        if (below > 0) {
-            k_chol_rows<<<(below + 7) / 8, 256, 0, d.stream>>>(S, n, kb, Ld);
-            d.launches++;
+        if (below <= 0) continue;
+        k_chol_rows<<<(below + 7) / 8, 256, 0, d.stream>>>(S, n, kb, Ld);
+        d.launches++;
+        const int t = (below + TT - 1) / TT;
+        if (t > 2) {
+            MLMD_CUDA(cudaEventRecord(d.ev_rows, d.stream));
+            MLMD_CUDA(cudaStreamWaitEvent(d.side, d.ev_rows, 0));
         }
-        if (below > 0) {
-            const int t = (below + TT - 1) / TT;
-            k_chol_trail<<<dim3(t, t), 256, 0, d.stream>>>(S, n, kb);
+        if (side_pending) {               // the previous panel's side update reaches block column kb+1
+            MLMD_CUDA(cudaStreamWaitEvent(d.stream, d.ev_trail, 0));
+            side_pending = false;
+        }
+        k_chol_trail<<<dim3(std::min(t, 2), t), 256, 0, d.stream>>>(S, n, kb, 0, 0);
+        d.launches++;
+        if (t > 2) {
+            k_chol_trail<<<dim3(t - 2, t - 2), 256, 0, d.side>>>(S, n, kb, 2, 2);
             d.launches++;
+            MLMD_CUDA(cudaEventRecord(d.ev_trail, d.side));
+            side_pending = true;
         }
     }
+    if (side_pending) MLMD_CUDA(cudaStreamWaitEvent(d.stream, d.ev_trail, 0));
     // X = L^{-1} by recursive doubling of inverted diagonal blocks, then Minv = X^H
     double* X = (double*)d.mem.get((size_t)n * n * 2 * sizeof(double));
     double* T = (double*)d.mem.get((size_t)n * n * 2 * sizeof(double));

@@ -167,6 +167,10 @@ struct Domain {
     int A_cap = 0;
     double* dense = nullptr;       // scratch for N_o x N_o FP64 work
     size_t dense_bytes = 0;
+    // look-ahead Cholesky: side stream for the trailing updates beyond the
+    // next block column, and its two ordering events (created on first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_rows = nullptr, ev_trail = nullptr;
 
     int64_t step = 0;              // steps since set_orbitals
     bool pa_psi = false;           // Pa holds <b|psi> of the current orbitals
