@@ -56,12 +56,12 @@ STAGE_SRC = os.path.join(ROOT, "paper_2509_00966_gb300", "csrc", "k_stage_tma.cu
 # reports no traffic.  Per orbital*gridpoint, so that a capture on fewer
 # orbitals scales to the benchmark's orbital count.
 STAGE_TRAFFIC = {
-    # (313.4 + 184.5) + (547.1 + 194.5) + (547.1 + 194.5) + (544.4 + 184.8) MB over
+    # (313.2 + 184.1) + (547.1 + 194.8) + (547.1 + 194.4) + (544.8 + 185.2) MB over
     # the four launches, 48^3 x 256 orbitals
-    "c1": {"src_sha16": "d48f7dca71e0a6fa", "bytes_per_unit": 677.6e6 / (48 ** 3 * 256)},
-    # (793.2 + 496.7) + (1333.1 + 506.4) + (1333.4 + 507.0) + (1329.9 + 497.8) MB over
+    "c1": {"src_sha16": "5a382b1bf69fc774", "bytes_per_unit": 677.7e6 / (48 ** 3 * 256)},
+    # (793.8 + 496.7) + (1332.3 + 506.4) + (1333.4 + 506.9) + (1330.4 + 497.9) MB over
     # the four launches, the c2 grid and projectors on 256 of its 1024 orbitals
-    "c2": {"src_sha16": "d48f7dca71e0a6fa", "bytes_per_unit": 1699.4e6 / (64 ** 3 * 256)},
+    "c2": {"src_sha16": "5a382b1bf69fc774", "bytes_per_unit": 1699.5e6 / (64 ** 3 * 256)},
 }
 
 
