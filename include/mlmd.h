@@ -294,7 +294,11 @@ MLMD_API mlmd_status mlmd_overlap_noalloc(int32_t precision, int64_t n_grid, int
  * stream; mlmd_profile_read synchronises that stream and returns the summed
  * device time and launch count of one kind since the last enable.  Enabling
  * (enable != 0) resets the totals. */
-enum { MLMD_KERNEL_STAGE = 0, MLMD_KERNEL_PROJECT = 1, MLMD_KERNEL_SCATTER = 2, MLMD_KERNEL_KINDS = 3 };
+/* MLMD_KERNEL_GEMM brackets a whole dense orbital GEMM (the Gram of
+ * mlmd_overlap and of the re-orthonormalisation, the update Psi M), with its
+ * operand split passes and partial-sum reductions. */
+enum { MLMD_KERNEL_STAGE = 0, MLMD_KERNEL_PROJECT = 1, MLMD_KERNEL_SCATTER = 2, MLMD_KERNEL_GEMM = 3,
+       MLMD_KERNEL_KINDS = 4 };
 MLMD_API mlmd_status mlmd_profile_enable(mlmd_domain_t dom, int32_t enable);
 MLMD_API mlmd_status mlmd_profile_read(mlmd_domain_t dom, int32_t kind, double* total_ms, uint64_t* launches);
 

@@ -382,7 +382,10 @@ void reorth(Domain& d, int kind) {
     MLMD_CUDA(cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, d.stream));
     MLMD_CUDA(cudaStreamSynchronize(d.stream));
     MLMD_REQUIRE(h_info == 0, MLMD_ERR_NUMERIC, "overlap matrix is not positive definite");
-    if (!launch_update_tc(d, d.psi, M, d.wa, kind == MLMD_ORTHO_CHOL)) launch_update(d, d.psi, M, d.wa);
+    {
+        ProfScope ps(d.prof, MLMD_KERNEL_GEMM, d.stream);
+        if (!launch_update_tc(d, d.psi, M, d.wa, kind == MLMD_ORTHO_CHOL)) launch_update(d, d.psi, M, d.wa);
+    }
     std::swap(d.psi, d.wa);
 }
 

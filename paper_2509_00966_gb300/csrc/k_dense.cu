@@ -480,6 +480,7 @@ __global__ void __launch_bounds__(256) k_trinv_x(const double* __restrict__ T, d
 }  // namespace
 
 void launch_overlap(Domain& d, const void* X, const void* Y, double scale, double* S) {
+    ProfScope ps(d.prof, MLMD_KERNEL_GEMM, d.stream);
     if (launch_overlap_tc(d, X, Y, scale, S)) return;    // tensor cores for the 16-bit GEMM modes
     const int no = d.desc.n_orb;
     const int tiles = (no + 31) / 32;

@@ -355,7 +355,7 @@ def overlap_noalloc(X, Y, scale, S, stream=None):
     return S
 
 
-KERNEL = {"stage": 0, "project": 1, "scatter": 2}
+KERNEL = {"stage": 0, "project": 1, "scatter": 2, "gemm": 3}
 
 
 def profile_enable(h, enable=True):
