@@ -388,11 +388,15 @@ __global__ void k_reduce_partials(const double* __restrict__ part, int nblk, int
 
 // ---------------------------------------------------------------------------
 // density and current: one warp per grid point, lanes over the orbital row,
-// warp-shuffle reduction over orbitals
+// warp-shuffle reduction over orbitals.  Complex64 rows sum each lane's
+// orbitals in FP32 (the occupations in the working type fR; a lane holds
+// ld/64 vectors, 16 at N_o = 1024) and reduce across the lanes in FP64:
+// FP64 arithmetic per orbital value cost milliseconds per call at Blackwell
+// Ultra's reduced FP64 rate.  Complex128 sums in FP64 throughout.
 // ---------------------------------------------------------------------------
 template <typename R, int ORDER>
 __global__ void __launch_bounds__(256) k_density_current(Geo G, const R* __restrict__ psi,
-                                                         const double* __restrict__ f,
+                                                         const double* __restrict__ f, const R* __restrict__ fR,
                                                          const double* __restrict__ Ak, R* __restrict__ rho,
                                                          R* __restrict__ jcur, double* __restrict__ Jpart) {
     constexpr int NC = Vec<R>::NC;
@@ -408,6 +412,43 @@ __global__ void __launch_bounds__(256) k_density_current(Geo G, const R* __restr
         const int z = (int)(gyz / G.ny);
         const Nb b[3] = {nbr(x, G.nx, 1), nbr(y, G.ny, G.nx), nbr(z, G.nz, (int64_t)G.nx * G.ny)};
         double r = 0.0, jj[3] = {0.0, 0.0, 0.0};
+        if constexpr (std::is_same<R, float>::value) {
+            float rf = 0.f, jf[3] = {0.f, 0.f, 0.f};
+            for (int j = lane; j < G.nv; j += 32) {
+                const Cx<R> c = ldg_c(rowp(psi, g, G.ld, j));
+                float fo[NC];
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    fo[k] = fR[j * NC + k];
+                    rf += fo[k] * (c.re[k] * c.re[k] + c.im[k] * c.im[k]);
+                }
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    const Cx<R> p1 = ldg_c(rowp(psi, g + b[ax].p1, G.ld, j));
+                    const Cx<R> m1 = ldg_c(rowp(psi, g + b[ax].m1, G.ld, j));
+                    Cx<R> dd;
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) {
+                        dd.re[k] = gk1 * (p1.re[k] - m1.re[k]);
+                        dd.im[k] = gk1 * (p1.im[k] - m1.im[k]);
+                    }
+                    if (ORDER == 4) {
+                        const Cx<R> p2 = ldg_c(rowp(psi, g + b[ax].p2, G.ld, j));
+                        const Cx<R> m2 = ldg_c(rowp(psi, g + b[ax].m2, G.ld, j));
+#pragma unroll
+                        for (int k = 0; k < NC; ++k) {
+                            dd.re[k] += gk2 * (p2.re[k] - m2.re[k]);
+                            dd.im[k] += gk2 * (p2.im[k] - m2.im[k]);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) jf[ax] += fo[k] * (c.re[k] * dd.im[k] - c.im[k] * dd.re[k]);
+                }
+            }
+            r = rf;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) jj[ax] = jf[ax];
+        } else
         for (int j = lane; j < G.nv; j += 32) {
             const Cx<R> c = ldg_c(rowp(psi, g, G.ld, j));
 #pragma unroll
@@ -694,14 +735,18 @@ void launch_density_current(Domain& d, const double* A, void* rho, void* j, doub
     const Geo G = make_geo(d);
     if (d.c64()) {
         if (d.desc.fd_order == 4)
-            k_density_current<float, 4><<<nblk, 256, 0, d.stream>>>(G, (const float*)d.psi, d.f, A, (float*)rho, (float*)j, Jpart);
+            k_density_current<float, 4><<<nblk, 256, 0, d.stream>>>(G, (const float*)d.psi, d.f, (const float*)d.fR, A, (float*)rho,
+                                                                (float*)j, Jpart);
         else
-            k_density_current<float, 2><<<nblk, 256, 0, d.stream>>>(G, (const float*)d.psi, d.f, A, (float*)rho, (float*)j, Jpart);
+            k_density_current<float, 2><<<nblk, 256, 0, d.stream>>>(G, (const float*)d.psi, d.f, (const float*)d.fR, A, (float*)rho,
+                                                                (float*)j, Jpart);
     } else {
         if (d.desc.fd_order == 4)
-            k_density_current<double, 4><<<nblk, 256, 0, d.stream>>>(G, (const double*)d.psi, d.f, A, (double*)rho, (double*)j, Jpart);
+            k_density_current<double, 4><<<nblk, 256, 0, d.stream>>>(G, (const double*)d.psi, d.f, (const double*)d.fR, A,
+                                                                 (double*)rho, (double*)j, Jpart);
         else
-            k_density_current<double, 2><<<nblk, 256, 0, d.stream>>>(G, (const double*)d.psi, d.f, A, (double*)rho, (double*)j, Jpart);
+            k_density_current<double, 2><<<nblk, 256, 0, d.stream>>>(G, (const double*)d.psi, d.f, (const double*)d.fR, A,
+                                                                 (double*)rho, (double*)j, Jpart);
     }
     d.launches++;
     MLMD_CUDA(cudaGetLastError());
